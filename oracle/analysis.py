@@ -1,0 +1,229 @@
+"""Oracle: post-processing of lattice fields into interface observables.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Restates, in plain numpy/scipy, the paper's definitions:
+
+* bulk pressure P_b = n c_s^2 + (G' e2 / 2) psi^2          (Sec. III A)
+* epsilon(e4) = (6 e4 - 2 e2) / (6 e4 + e2)                 (eq. eps_moments)
+* Maxwell-like coexistence: int_{n_g}^{n_l} dn psi'/psi^(eps+1) (p0 - P_b) = 0
+  with P_b(n_g) = P_b(n_l) = p0                              (eq. SCMaxwell)
+* flat-interface profile slope (dpsi/dx)^2                 (eq. PSIProfile)
+* second-order surface tension estimate                     (eq. scsigma)
+* analytic SC Tolman length                                 (eq. SCTolmanFlat)
+* flat sigma_0 = int (P_N - P_T) dx                         (eq. sigma0pnpt)
+* z_s = first moment of P_N - P_T                           (eq. ZSDef)
+* z_e from Gamma(z_e) = 0, delta = z_e - z_s                 (eq. zemzs)
+* delta = Gamma(z_s) / (n_l - n_g)                          (eq. deltaads)
+* equimolar radius                                          (Sec. V B, Laplace)
+* generalized sigma[R] and the surface of tension           (Sec. III B)
+
+Readings where the paper is silent (each used identically by the package's
+own post-processing):
+* a flat periodic slab has several interfaces; the integrals are lattice sums
+  over windows centred on each interface, window borders half way between
+  neighbouring interfaces (in bulk);
+* site x stands for the cell [x - 1/2, x + 1/2]; n_l and n_g are the measured
+  densities at the liquid and gas ends of the window;
+* the x axis of a window is oriented from liquid to gas when forming delta
+  (the orientation that gives eq. SCTolmanFlat its sign).
+"""
+from __future__ import annotations
+
+from math import exp
+
+import numpy as np
+from scipy import integrate, optimize
+
+CS2 = 1.0 / 3.0
+
+
+def psi_exp(n):
+    return np.exp(-1.0 / np.asarray(n, dtype=np.float64))
+
+
+def dpsi_exp(n):
+    n = np.asarray(n, dtype=np.float64)
+    return np.exp(-1.0 / n) / (n * n)
+
+
+def psi_eps_fn(eps):
+    def f(n):
+        n = np.asarray(n, dtype=np.float64)
+        return (n / (eps + n)) ** (1.0 / eps)
+
+    def df(n):
+        n = np.asarray(n, dtype=np.float64)
+        return (n / (eps + n)) ** (1.0 / eps) / (n * (eps + n))
+    return f, df
+
+
+def epsilon_of_e4(e4, e2=1.0):
+    """eq. ``eps_moments``."""
+    return (6.0 * e4 - 2.0 * e2) / (6.0 * e4 + e2)
+
+
+def bulk_pressure(n, Gp, e2=1.0, psi=psi_exp):
+    """P_b = n c_s^2 + (G' e2 / 2) psi^2 (Sec. III A, with G' = G c_s^2 in the
+    paper's convention or G in the literal one)."""
+    n = np.asarray(n, dtype=np.float64)
+    return n * CS2 + 0.5 * Gp * e2 * psi(n) ** 2
+
+
+def critical_coupling(e2=1.0, psi=psi_exp, dpsi=dpsi_exp, n0=1.0):
+    """(G'_c, n_c): where dP_b/dn = d^2P_b/dn^2 = 0 (found numerically)."""
+    def eqs(v):
+        G, n = v
+        h = 1e-5
+        p = lambda m: bulk_pressure(m, G, e2, psi)
+        d1 = (p(n + h) - p(n - h)) / (2 * h)
+        d2 = (p(n + h) - 2 * p(n) + p(n - h)) / (h * h)
+        return [d1, d2]
+    sol = optimize.fsolve(eqs, [-2.4, n0], xtol=1e-13)
+    return float(sol[0]), float(sol[1])
+
+
+def coexistence(Gp, eps=0.0, e2=1.0, psi=psi_exp, dpsi=dpsi_exp, guess=(0.2, 2.0)):
+    """(n_g, n_l, p0) from eq. ``SCMaxwell``: equal pressure and a vanishing
+    integral with measure dn psi'/psi^(eps+1)."""
+    def P(n):
+        return bulk_pressure(n, Gp, e2, psi)
+
+    def integral(ng, nl, p0):
+        fn = lambda m: dpsi(m) / psi(m) ** (eps + 1.0) * (p0 - P(m))
+        return integrate.quad(fn, ng, nl, epsabs=1e-14, epsrel=1e-13, limit=400)[0]
+
+    def eqs(v):
+        ng, nl = v
+        p0 = P(ng)
+        return [P(nl) - p0, integral(ng, nl, p0)]
+    ng, nl = optimize.fsolve(eqs, list(guess), xtol=1e-13)
+    return float(ng), float(nl), float(P(ng))
+
+
+def _profile_slope2(n, ng, p0, Gp, eps, e2, psi, dpsi):
+    """(dpsi/dx)^2 at density n from eq. ``PSIProfile``."""
+    fn = lambda m: dpsi(m) / psi(m) ** (eps + 1.0) * (p0 - bulk_pressure(m, Gp, e2, psi))
+    I = integrate.quad(fn, ng, n, epsabs=1e-15, epsrel=1e-12, limit=400)[0]
+    return 8.0 * (1.0 - eps) / (Gp * e2) * psi(n) ** eps * I
+
+
+def sigma_second_order(Gp, e4, eps=0.0, e2=1.0, psi=psi_exp, dpsi=dpsi_exp, guess=(0.2, 2.0)):
+    """eq. ``scsigma``: sigma0 ~ -(G' e4 / 2) int (dpsi/dx)^2 dx, with the
+    integral over x rewritten over n through |dpsi/dx| dx = psi'(n) dn."""
+    ng, nl, p0 = coexistence(Gp, eps, e2, psi, dpsi, guess)
+    g = lambda m: dpsi(m) * np.sqrt(max(_profile_slope2(m, ng, p0, Gp, eps, e2, psi, dpsi), 0.0))
+    I = integrate.quad(g, ng, nl, epsabs=1e-14, epsrel=1e-10, limit=400)[0]
+    return -0.5 * Gp * e4 * I
+
+
+def tolman_sc(Gp, sigma0, delta0_hat, ng, nl, psi=psi_exp):
+    """eq. ``SCTolmanFlat``: delta ~ -(G'/(2 sigma0)) delta0_hat
+    [psi^2(n_l) - psi^2(n_g)]."""
+    return -(Gp / (2.0 * sigma0)) * delta0_hat * (float(psi(nl)) ** 2 - float(psi(ng)) ** 2)
+
+
+# --- flat interfaces ------------------------------------------------------------
+def _line_profiles(P, n, D):
+    """Average over y (and z) to 1D profiles along x: n(x), P_N = P^xx,
+    P_T = P^yy."""
+    axes = (0, 1)
+    nx_ = n.mean(axis=axes)
+    PN = P[0].mean(axis=axes)
+    PT = P[2 if D == 2 else 3].mean(axis=axes)
+    return nx_, PN, PT
+
+
+def interfaces(n1d):
+    """Positions i where the profile crosses the mid density between i and
+    i+1 (periodic), with +1 for rising (gas->liquid) and -1 for falling."""
+    mid = 0.5 * (n1d.max() + n1d.min())
+    s = np.sign(n1d - mid)
+    out = []
+    L = len(n1d)
+    for i in range(L):
+        a, b = s[i], s[(i + 1) % L]
+        if a != b and a != 0 and b != 0:
+            out.append((i, 1 if b > a else -1))
+    return out
+
+
+def flat_interface_windows(n1d):
+    """Windows [a, b] (inclusive, may wrap) around each interface, bounded
+    half way between neighbouring interfaces."""
+    ifs = interfaces(n1d)
+    L = len(n1d)
+    k = len(ifs)
+    wins = []
+    for q in range(k):
+        i, d = ifs[q]
+        prev = ifs[q - 1][0]
+        nxt = ifs[(q + 1) % k][0]
+        gap_prev = (i - prev) % L if k > 1 else L
+        gap_next = (nxt - i) % L if k > 1 else L
+        a = i - gap_prev // 2 + 1
+        b = i + gap_next // 2
+        wins.append((a, b, d))
+    return wins
+
+
+def flat_observables(P, n, D=2):
+    """sigma_0, z_s, z_e, delta (both definitions) per interface of a flat
+    periodic slab (gradients along x)."""
+    n1, PN, PT = _line_profiles(P, n, D)
+    L = len(n1)
+    res = []
+    for a, b, d in flat_interface_windows(n1):
+        xs = np.arange(a, b + 1)
+        idx = xs % L
+        dP = PN[idx] - PT[idx]
+        sig = float(np.sum(dP))
+        zs = float(np.sum(xs * dP) / sig)
+        nn = n1[idx]
+        if d > 0:   # gas -> liquid along +x
+            ng, nl = nn[0], nn[-1]
+            ze = (b + 0.5) - float(np.sum((nn - ng) / (nl - ng)))
+        else:       # liquid -> gas along +x
+            nl, ng = nn[0], nn[-1]
+            ze = (a - 0.5) + float(np.sum((nn - ng) / (nl - ng)))
+        orient = -d   # +1 when x runs from liquid to gas
+        delta = orient * (ze - zs)
+        # Gamma(z_s) with the same bulk values, x oriented liquid -> gas
+        M = float(np.sum(nn))
+        if d > 0:
+            gamma = M - ng * (zs - (a - 0.5)) - nl * ((b + 0.5) - zs)
+        else:
+            gamma = M - nl * (zs - (a - 0.5)) - ng * ((b + 0.5) - zs)
+        delta_ads = gamma / (nl - ng)
+        res.append({"sigma": sig, "z_s": zs, "z_e": ze, "delta": delta,
+                    "delta_ads": delta_ads, "n_l": float(nl), "n_g": float(ng),
+                    "window": (a, b), "rising": d > 0})
+    return res
+
+
+def flat_sigma(P, n, D=2):
+    """sigma_0 = (sum over the periodic line of P_N - P_T) / #interfaces."""
+    n1, PN, PT = _line_profiles(P, n, D)
+    k = len(interfaces(n1))
+    if k == 0:
+        return float("nan")
+    return float(np.sum(PN - PT)) / k
+
+
+# --- curved interfaces ----------------------------------------------------------
+def equimolar_radius(n, n_in, n_out):
+    """eq. (Laplace paragraph): pi R^2 n_in + (L^2 - pi R^2) n_out = M (2D), the
+    3D analogue with 4/3 pi R^3 (n_in is the inside density, droplet or
+    bubble)."""
+    M = float(np.sum(n))
+    V = n.size
+    if n.shape[0] == 1:
+        return float(np.sqrt((M - V * n_out) / (np.pi * (n_in - n_out))))
+    return float(np.cbrt((M - V * n_out) / (4.0 / 3.0 * np.pi * (n_in - n_out))))
+
+
+def laplace_fit(inv_R, dP):
+    """Least-squares slope and intercept of dP vs 1/R (d-1 = 1 in 2D)."""
+    A = np.vstack([np.asarray(inv_R), np.ones(len(inv_R))]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, np.asarray(dP), rcond=None)
+    return float(slope), float(icpt)
