@@ -1,0 +1,365 @@
+"""Benchmark: fused Shan-Chen lattice-Boltzmann steps on GB300.
+
+Workload (the headline configuration): D3Q19, E8 forcing stencil (92
+vectors), 256^3 periodic box with one bubble of radius 40 (rho 0.15 inside,
+1.9 outside, tanh width 2), shifted binary32 populations, G = -5 (force
+without c_s^2), tau = 1.  One step = psi, stencil force, BGK + Guo
+collision and streaming over all 16.8 M nodes.  Populations (2 x 1.27 GB)
+are far larger than L2, so no flush is needed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  ``value`` is MLUPS over all ranks (one independent
+replica per GPU: the workload has no exchange step on one device), timed
+with CUDA events on the library's stream between barriers, max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline (D3Q19 E8, FP32 vs FP64); adjoint steps/s at 1e-3 sigma"
+NX = NY = NZ = 256
+RADIUS = 40.0
+WORKLOAD = ("D3Q19 E8 (92-vector forcing stencil) 256^3 periodic, bubble R=40 "
+            "(rho_in 0.15, rho_out 1.9, tanh width 2), shifted FP32, G=-5 literal, tau=1")
+# algorithmic bytes per node update and kernel (population read + write,
+# plus the psi field where a kernel reads or writes it)
+ALG_BYTES = {"fused": 2 * 19 * 4, "collide": 2 * 19 * 4 + 4, "psi": 19 * 4 + 4}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_23647_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        with open(p) as fh:
+            d = json.loads("".join(l for l in fh if not l.startswith("#")))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("src_sha") != _src_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, 0, 1
+
+
+def reduce_max(dist, value, device=None):
+    """Max over ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload_rho():
+    import lbinputs as L
+    return L.tanh_sphere(NX, NY, NZ, RADIUS, 0.15, 1.9, 2.0)
+
+
+# ---------------------------------------------------------------------------
+def oracle_mlups(sub, steps):
+    """The FP64 oracle as it stands, single thread, on a centred sub-box of
+    the workload (same lattice, stencil and physics); returns MLUPS."""
+    import lbinputs as L
+    import oracle
+    rho = _workload_rho()
+    c = NX // 2
+    h = sub // 2
+    box = np.ascontiguousarray(rho[c - h:c - h + sub, c - h:c - h + sub, c - h:c - h + sub])
+    o = oracle.Oracle("D3Q19", box.shape, L.E8_3D.groups, tau=1.0, G=-5.0)
+    o.init_equilibrium(box)
+    o.step(1)  # warm
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return box.size * steps / dt / 1e6, dt
+
+
+def run_reference(args, dist, rank, ws):
+    if rank != 0:
+        return
+    # each step: one oracle step of a centred sub-box sized so the whole
+    # --steps/--warmup run stays within about two minutes
+    per_node = 2.8e-6
+    budget = 100.0
+    sub = int(max(8, min(64, (budget / (per_node * max(1, args.steps + args.warmup))) ** (1 / 3))))
+    import lbinputs as L
+    import oracle
+    rho = _workload_rho()
+    c, h = NX // 2, sub // 2
+    box = np.ascontiguousarray(rho[c - h:c - h + sub, c - h:c - h + sub, c - h:c - h + sub])
+    o = oracle.Oracle("D3Q19", box.shape, L.E8_3D.groups, tau=1.0, G=-5.0)
+    o.init_equilibrium(box)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = box.size * args.steps / dt / 1e6
+    sample = f"FP64 C oracle, 1 thread, {sub}^3 centred sub-box of the workload per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def run_gb300(args, dist, rank, ws):
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import lbinputs as L
+    import paper_2505_23647_gb300 as P
+
+    stream = torch.cuda.current_stream(dev)
+    N = NX * NY * NZ
+    rho = _workload_rho()
+    # pinned host copy of the input (used by the end-to-end measurement)
+    rho_pinned = torch.empty(rho.size, dtype=torch.float64, pin_memory=True)
+    rho_pinned.numpy()[:] = rho.ravel()
+
+    lat = P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), L.E8_3D.bases,
+                    L.E8_3D.weights, precision="fp32", tau=1.0, G=-5.0,
+                    stream=stream.cuda_stream)
+    lat.step(args.warmup)
+    if lat.sync() != P.LB_OK:
+        raise RuntimeError("unstable during warm-up")
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis else str(local)
+    sampler = ClockSampler(smi_index)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lat.launches()
+    P.lb_timing(lat.ctx, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kt = P.lb_timing_read(lat.ctx)
+    P.lb_timing(lat.ctx, 0)
+    launches = lat.launches() - launches0
+    if lat.sync() != P.LB_OK:
+        raise RuntimeError("unstable during the timed steps")
+    ms_max = reduce_max(dist, ms, dev)
+    value = N * args.steps * ws / (ms_max * 1e3)
+
+    # dominant kernel of the step and its roofline
+    kind = max((k for k in kt if kt[k][1]), key=lambda k: kt[k][0])
+    kms, kn = kt[kind]
+    peak, peak_src = _peaks()
+    achieved = ALG_BYTES[kind] * N / (kms / kn * 1e-3) / 1e9
+    traffic = _traffic(kind)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kind,
+                "alg_bytes_per_node": ALG_BYTES[kind], "peak_source": f"{peak_src} hbm_gbs",
+                "kernel_ms_avg": kms / kn,
+                "step_kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt.items() if v[1]}}
+    obs = lat.observables()
+    lat.close()
+
+    # FP64 path on the same workload (fewer steps; binary64 arithmetic)
+    fp64 = None
+    if not args.no_fp64:
+        lat64 = P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), L.E8_3D.bases,
+                          L.E8_3D.weights, precision="fp64", tau=1.0, G=-5.0,
+                          stream=stream.cuda_stream)
+        lat64.step(2)
+        lat64.sync()
+        k64 = max(4, args.steps // 20)
+        P.lb_timing(lat64.ctx, 1)
+        e0.record(stream)
+        lat64.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        kt64 = P.lb_timing_read(lat64.ctx)
+        lat64.close()
+        v64 = N * k64 / (ms64 * 1e3)
+        fp64 = {"value": v64, "unit": "MLUPS", "steps": k64, "ms_per_step": ms64 / k64,
+                "hbm_frac": (2 * 19 * 8 + 16) * v64 * 1e6 / 1e9 / peak,
+                "step_kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt64.items() if v[1]}}
+
+    # end to end through the C ABI with host buffers: create from the pinned
+    # host density (H2D), K steps, read back the density (D2H) and the
+    # observables
+    e2e = None
+    if not args.no_e2e:
+        rho_out = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = P.lb_create(P.make_params("D3Q19", (NX, NY, NZ), "fp32", 1.0, -5.0),
+                          rho_pinned.numpy(), None, stream.cuda_stream)
+        P.lb_set_stencil(ctx, 3, L.E8_3D.bases, L.E8_3D.weights)
+        P.lb_step(ctx, args.steps)
+        P._check(P._lib.lb_get_fields(P._vp(ctx), P._ptr(rho_out.numpy()), None), "lb_get_fields")
+        o2 = P.lb_observables(ctx)
+        t1 = time.perf_counter()
+        P.lb_destroy(ctx)
+        dt = reduce_max(dist, t1 - t0, dev)
+        e2e = {"value": N * args.steps * ws / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": N * 8 / args.steps,
+               "d2h_bytes_per_step": (N * 8 + 88) / args.steps,
+               "seconds": dt, "mass": o2["mass"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sub, csteps = 64, 12
+        v, dt = oracle_mlups(sub, csteps)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{csteps} steps of the FP64 C oracle on the {sub}^3 centred sub-box "
+                         f"of the workload ({dt:.1f} s, 1 thread)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": "D3Q19", "stencil": "E8 (92 vectors)",
+                       "nodes": N, "precision": "fp32 shifted (g = f - w rho0)",
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (2 x 1.27 GB populations)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "fp64": fp64,
+            "observables": {"mass": obs["mass"], "umax": obs["umax"],
+                            "rho_min": obs["rho_min"], "rho_max": obs["rho_max"]},
+        }
+        print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    dist, rank, ws = _dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist, rank, ws)
+        else:
+            run_gb300(args, dist, rank, ws)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * sclbm.h -- C ABI of the GB300 (sm_103a) Shan-Chen multiphase
+ * lattice-Boltzmann library with extended, tunable forcing stencils
+ * (Lulli & Ching, "Higher-order Tuning of Interface Physics in Multiphase
+ * Lattice Boltzmann").
+ *
+ * Model (one step, every node x of a fully periodic lattice; Sec. II and
+ * Sec. III A of the paper):
+ *   n = sum_i f_i,  psi = exp(-1/n)
+ *   F(x) = -G' psi(x) sum_a W(|e_a|^2) psi(x + e_a) e_a          (eq. sc_f)
+ *   u = (sum_i f_i xi_i + F/2) / n                     (force-shifted u)
+ *   f_i* = f_i - (f_i - f_i^eq(n,u))/tau + F_i (Guo, T = 2uF)
+ *                                        (eqs. lbm, omega_i, f_eq, GuoForcing)
+ *   f_i(x + xi_i, t+1) = f_i*(x)                                 (streaming)
+ * G' = G for LB_G_LITERAL (the force written without c_s^2, the library's
+ * default) or G c_s^2 = G/3 for LB_G_TIMES_CS2 (eq. sc_f as printed).
+ *
+ * Conventions shared by every call
+ *   - Fields are x-fastest: index s = (z*ny + y)*nx + x.  2D lattices have
+ *     nz = 1.  Vector fields are component-major: [D][N].
+ *   - Populations ("state") are component-major [Q][N] float64, f_i(x) at
+ *     integer time after streaming.  Velocity order, D2Q9:
+ *       0 (0,0) 1 (1,0) 2 (0,1) 3 (-1,0) 4 (0,-1) 5 (1,1) 6 (-1,1)
+ *       7 (-1,-1) 8 (1,-1)
+ *     D3Q19:
+ *       0 (0,0,0) 1 (1,0,0) 2 (-1,0,0) 3 (0,1,0) 4 (0,-1,0) 5 (0,0,1)
+ *       6 (0,0,-1) 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0)
+ *       11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1)
+ *       16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1)
+ *   - Host pointers are caller-owned and only read/written during the call.
+ *     Device memory is owned by the context until lb_destroy.
+ *   - Every call returns an lb_status; no C++ exception crosses the ABI.
+ *     A context is not thread-safe: use one context per host thread.
+ *   - Precision LB_FP64 follows the exact rounding order documented below,
+ *     so results equal a reference that evaluates the same expressions
+ *     in IEEE binary64 (round to nearest, no FMA contraction) bit for bit.
+ *     LB_FP32_SHIFTED stores g_i = f_i - w_i rho0 in binary32 and computes
+ *     in binary32 (density within 1e-5 relative of binary64 over 100 steps
+ *     on the tested workloads).
+ *
+ * FP64 rounding order (a reading of the model; every binary64 operation
+ * below is rounded to nearest):
+ *   n = ((f_0 + f_1) + f_2) + ...;  psi = RN(exp(RN(-1/n))), exp correctly
+ *   rounded;  acc^mu += (W_a*(psi(x+e_a) - psi(x-e_a))) * e_a^mu over the
+ *   canonical (e,-e) pairs of lb_expand_stencil;  F = (-G'*psi(x))*acc;
+ *   j^mu = sum_i f_i xi_i^mu in table order;  u = (j + 0.5*F)/n;
+ *   uu = u.u, uF = u.F, cu = xi.u, cF = xi.F summed x, y, z;
+ *   f_eq = (w_i*n)*(((1 + 3*cu) + 4.5*(cu*cu)) - 1.5*uu);
+ *   S = ((1 - 1/(2 tau))*w_i)*((3*cF + 9*(cu*cF)) - 3*uF);
+ *   f* = (f - (1/tau)*(f - f_eq)) + S.
+ */
+#ifndef SCLBM_H
+#define SCLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lb_status {
+    LB_OK = 0,
+    LB_EINVAL = 1,        /* bad argument or parameter */
+    LB_ENOMEM = 2,        /* device or host allocation failed */
+    LB_ECUDA = 3,         /* a CUDA runtime call failed (see lb_last_cuda_error) */
+    LB_EUNSTABLE = 4,     /* a node had n <= 0 or NaN (see lb_obs.error_step) */
+    LB_EUNSUPPORTED = 5,  /* valid request this build does not cover */
+    LB_ESTATE = 6         /* call out of order, e.g. lb_step before lb_set_stencil */
+} lb_status;
+
+enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
+enum { LB_FP64 = 0, LB_FP32_SHIFTED = 1 };
+enum { LB_G_LITERAL = 0, LB_G_TIMES_CS2 = 1 };
+enum { LB_PSI_EXP = 0 };
+
+/* Largest number of (e,-e) pairs and largest |component| of a stencil vector. */
+#define LB_MAX_PAIRS 160
+#define LB_MAX_RADIUS 4
+
+typedef struct lb_params {
+    int lattice;        /* LB_D2Q9 or LB_D3Q19 */
+    int nx, ny, nz;     /* periodic lattice size; nz = 1 for D2Q9; each >= 1 */
+    int precision;      /* LB_FP64 or LB_FP32_SHIFTED */
+    double tau;         /* BGK relaxation time, > 1/2 */
+    double G;           /* coupling constant (G < 0 separates phases) */
+    int g_convention;   /* LB_G_LITERAL or LB_G_TIMES_CS2 */
+    int psi_kind;       /* LB_PSI_EXP: psi = exp(-1/n) */
+    double psi_eps;     /* reserved, 0 */
+    double rho0_shift;  /* rho0 of the FP32 shift g_i = f_i - w_i rho0 */
+} lb_params;
+
+typedef struct lb_stencil_info {
+    int n_groups;       /* symmetry groups */
+    int n_pairs;        /* (e,-e) pairs = n_vectors / 2 */
+    int n_vectors;      /* N_e of the paper's tables */
+    int radius;         /* max |component| */
+    double e2, e4, e6, e8;   /* <x^2>, <x^2y^2>, <x^4y^2>/3, <x^4y^4>/9 */
+    double iso_residual[4];  /* max |M_2k - e_2k Delta_2k| for 2k = 4,6,8,10 */
+} lb_stencil_info;
+
+typedef struct lb_obs {
+    double mass;        /* sum_x n */
+    double mom[3];      /* sum_x (j + F/2) */
+    double umax;        /* max_x |u| */
+    double rho_min, rho_max;
+    long long step;     /* steps taken since lb_create */
+    long long error_step;    /* first step whose density check failed, -1 if none */
+    long long exp_ambiguous; /* FP64 exp evaluations flagged as too close to a
+                                rounding boundary to certify (expected 0) */
+} lb_obs;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Human-readable name of a status code (static storage). */
+const char *lb_status_str(lb_status s);
+
+/* Last CUDA error string seen by this thread's failing call ("" if none). */
+const char *lb_last_cuda_error(void);
+
+/* Fill *p with defaults: D2Q9 64x64x1, FP64, tau 1, G -5, literal G,
+ * psi = exp(-1/n), rho0_shift 1. */
+lb_status lb_params_default(lb_params *p);
+
+/* Expand symmetry groups into the canonical (e,-e) pair list (host only, no
+ * GPU needed).  Each group is one base vector (dim ints, row-major in
+ * base_vectors) whose orbit under coordinate permutations and sign flips is
+ * the group (Sec. III A); W[g] is its weight W(|e|^2).  Pair order: groups by
+ * |e|^2, ties by the sorted absolute base components in descending
+ * lexicographic order; inside a group the representatives (first non-zero
+ * component positive) in descending lexicographic order of (e_x,e_y,e_z).
+ * Writes up to max_pairs pairs to pair_vec [3 per pair, z = 0 in 2D] and
+ * pair_w, the count to *n_pairs, and moments to *info (either may be NULL).
+ * LB_EINVAL: dim not 2/3, n_groups < 1, a zero or repeated group, a
+ * component beyond LB_MAX_RADIUS, or more than max_pairs pairs. */
+lb_status lb_expand_stencil(int dim, int n_groups, const int *base_vectors,
+                            const double *W, int max_pairs, int *pair_vec,
+                            double *pair_w, int *n_pairs, lb_stencil_info *info);
+
+/* Create a context: allocate device state and set f_i = f_i^eq(rho, u)
+ * (u = 0 if u_init is NULL) on every node (reading: the paper does not state
+ * the initial condition; equilibrium at rest is used).  rho_init: host [N]
+ * float64; u_init: host [D][N] float64 or NULL.  cuda_stream: a
+ * cudaStream_t all work of the context is ordered on, or NULL for a stream
+ * the context creates.  On success *out owns device memory until
+ * lb_destroy.  LB_EINVAL for bad parameters, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_create(const lb_params *p, const double *rho_init,
+                    const double *u_init, void *cuda_stream, lb_ctx **out);
+
+/* Free the context's device memory (synchronizes its stream).  NULL is a
+ * no-op. */
+lb_status lb_destroy(lb_ctx *ctx);
+
+/* Set the forcing stencil (eq. sc_f): groups as in lb_expand_stencil.
+ * Weights are used as given (no renormalisation).  *info may be NULL.
+ * LB_EINVAL for the lb_expand_stencil errors or a radius larger than the
+ * lattice allows (each dimension must be >= 1; any radius wraps
+ * periodically).  Must be called before lb_step. */
+lb_status lb_set_stencil(lb_ctx *ctx, int n_groups, const int *base_vectors,
+                         const double *W, lb_stencil_info *info);
+
+/* Advance nsteps >= 0 steps.  Asynchronous on the context's stream: returns
+ * once the work is enqueued.  Density checks (n > 0, not NaN) run inside the
+ * kernels; a failure is reported by lb_sync / lb_observables as
+ * LB_EUNSTABLE with the first failing step in lb_obs.error_step.
+ * LB_ESTATE if no stencil is set. */
+lb_status lb_step(lb_ctx *ctx, int nsteps);
+
+/* Wait for the context's stream.  LB_EUNSTABLE if a density check failed
+ * since lb_create, else LB_OK (or LB_ECUDA). */
+lb_status lb_sync(lb_ctx *ctx);
+
+/* Observables of the current state with FP64 accumulation (compensated
+ * double-double sums in a fixed order, rounded once): mass, momentum
+ * sum(j + F/2), max |u|, min/max n.  Synchronous.  Returns LB_EUNSTABLE
+ * (with *out filled) if a density check failed. */
+lb_status lb_observables(lb_ctx *ctx, lb_obs *out);
+
+/* Lattice pressure tensor (Appendices E and F) including the ideal part
+ * n c_s^2 delta, evaluated in binary64 from the current state.  out: host
+ * [C][N] float64, C = 3 (xx, xy, yy) in 2D or 6 (xx, xy, xz, yy, yz, zz) in
+ * 3D.  Groups covered: regular (k,0[,0]), (k,k[,0]), (k,k,k) for k <= 4 and
+ * the irregular (2,1[,0]), (2,1,1), (2,2,1); others give LB_EUNSUPPORTED.
+ * Synchronous. */
+lb_status lb_pressure_tensor(lb_ctx *ctx, double *out);
+
+/* Density [N] and velocity u = (j + F/2)/n [D][N] of the current state
+ * (either pointer may be NULL).  Synchronous. */
+lb_status lb_get_fields(lb_ctx *ctx, double *rho, double *u);
+
+/* Current populations f_i(x) as float64 [Q][N] (FP32 states are widened and
+ * the shift w_i rho0 added back).  Synchronous. */
+lb_status lb_get_state(lb_ctx *ctx, double *f);
+
+/* Replace the populations with f [Q][N] float64 (rounded to binary32 after
+ * removing the shift in FP32 mode).  Synchronous. */
+lb_status lb_set_state(lb_ctx *ctx, const double *f);
+
+/* Diagnostic: y[k] = RN(exp(x[k])) for k < n, evaluated on the GPU by the
+ * same correctly rounded binary64 exp the FP64 step uses.  Host arrays.
+ * Synchronous.  *n_ambiguous (may be NULL) receives the number of inputs
+ * whose rounding could not be certified. */
+lb_status lb_exp_cr(const double *x, double *y, long long n,
+                    long long *n_ambiguous);
+
+/* Number of kernels this context has launched (for launch accounting). */
+long long lb_kernel_launches(const lb_ctx *ctx);
+
+/* Kernel kinds of the step, for lb_timing_read. */
+enum { LB_KERNEL_PSI = 0, LB_KERNEL_COLLIDE = 1, LB_KERNEL_FUSED = 2, LB_KERNEL_OTHER = 3,
+       LB_KERNEL_KINDS = 4 };
+
+/* Per-kernel timing: enable = 1 resets the accumulators and brackets every
+ * subsequent step kernel with CUDA events recorded on the context's stream;
+ * enable = 0 stops recording (accumulators are kept). */
+lb_status lb_timing(lb_ctx *ctx, int enable);
+
+/* Wait for the stream and return, per kernel kind, the summed device time
+ * in milliseconds (ms[LB_KERNEL_KINDS]) and the number of launches timed
+ * (launches[LB_KERNEL_KINDS]); either pointer may be NULL. */
+lb_status lb_timing_read(lb_ctx *ctx, double *ms, long long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCLBM_H */

@@ -1,0 +1,324 @@
+"""Python binding of the GB300 Shan-Chen lattice-Boltzmann library.
+
+Thin ctypes marshalling over the C ABI of ``include/sclbm.h`` (same names:
+``lb_create``, ``lb_set_stencil``, ``lb_step``, ``lb_observables``,
+``lb_pressure_tensor``, ...).  Every step of the model runs in the CUDA
+kernels of ``_lib/libsclbm.so``; this module only converts arguments (numpy
+arrays or CPU torch tensors in, numpy arrays out) and raises ``LbError`` for
+a non-OK status.  There is no CPU fallback: importing the package without the
+built library raises ``ImportError``.
+
+``Lattice`` is a small convenience owner of one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsclbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"CUDA library not built ({LIB_PATH} missing); run "
+        "`python -c 'import __graft_entry__ as g; g.build()'` or "
+        "`python paper_2505_23647_gb300/build.py`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_EUNSUPPORTED, LB_ESTATE = range(7)
+LB_D2Q9, LB_D3Q19 = 0, 1
+LB_FP64, LB_FP32_SHIFTED = 0, 1
+LB_G_LITERAL, LB_G_TIMES_CS2 = 0, 1
+LB_PSI_EXP = 0
+LB_MAX_PAIRS = 160
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("precision", ctypes.c_int), ("tau", ctypes.c_double),
+                ("G", ctypes.c_double), ("g_convention", ctypes.c_int),
+                ("psi_kind", ctypes.c_int), ("psi_eps", ctypes.c_double),
+                ("rho0_shift", ctypes.c_double)]
+
+
+class lb_stencil_info(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int), ("n_pairs", ctypes.c_int),
+                ("n_vectors", ctypes.c_int), ("radius", ctypes.c_int),
+                ("e2", ctypes.c_double), ("e4", ctypes.c_double), ("e6", ctypes.c_double),
+                ("e8", ctypes.c_double), ("iso_residual", ctypes.c_double * 4)]
+
+
+class lb_obs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("mom", ctypes.c_double * 3),
+                ("umax", ctypes.c_double), ("rho_min", ctypes.c_double),
+                ("rho_max", ctypes.c_double), ("step", ctypes.c_longlong),
+                ("error_step", ctypes.c_longlong), ("exp_ambiguous", ctypes.c_longlong)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+_SIGS = {
+    "lb_status_str": ([ctypes.c_int], ctypes.c_char_p),
+    "lb_last_cuda_error": ([], ctypes.c_char_p),
+    "lb_params_default": ([ctypes.POINTER(lb_params)], ctypes.c_int),
+    "lb_expand_stencil": ([ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_int, _ip, _dp, _ip,
+                           ctypes.POINTER(lb_stencil_info)], ctypes.c_int),
+    "lb_create": ([ctypes.POINTER(lb_params), _dp, _dp, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "lb_destroy": ([_vp], ctypes.c_int),
+    "lb_set_stencil": ([_vp, ctypes.c_int, _ip, _dp, ctypes.POINTER(lb_stencil_info)], ctypes.c_int),
+    "lb_step": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lb_sync": ([_vp], ctypes.c_int),
+    "lb_observables": ([_vp, ctypes.POINTER(lb_obs)], ctypes.c_int),
+    "lb_pressure_tensor": ([_vp, _dp], ctypes.c_int),
+    "lb_get_fields": ([_vp, _dp, _dp], ctypes.c_int),
+    "lb_get_state": ([_vp, _dp], ctypes.c_int),
+    "lb_set_state": ([_vp, _dp], ctypes.c_int),
+    "lb_exp_cr": ([_dp, _dp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "lb_kernel_launches": ([_vp], ctypes.c_longlong),
+    "lb_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lb_timing_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+class LbError(RuntimeError):
+    def __init__(self, status, where=""):
+        msg = _lib.lb_status_str(status).decode()
+        cu = _lib.lb_last_cuda_error().decode()
+        if status == LB_ECUDA and cu:
+            msg += f" ({cu})"
+        super().__init__(f"{where}: {msg}" if where else msg)
+        self.status = status
+
+
+def _check(status, where):
+    if status != LB_OK:
+        raise LbError(status, where)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    if hasattr(a, "detach"):          # torch tensor (CPU)
+        a = a.detach().cpu().numpy()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def lb_params_default():
+    p = lb_params()
+    _check(_lib.lb_params_default(ctypes.byref(p)), "lb_params_default")
+    return p
+
+
+def make_params(lattice="D2Q9", shape=(64, 64), precision="fp64", tau=1.0, G=-5.0,
+                convention="literal", rho0_shift=1.0):
+    """lb_params from Python values; shape is (nx, ny) or (nx, ny, nz)."""
+    p = lb_params_default()
+    p.lattice = {"D2Q9": LB_D2Q9, "D3Q19": LB_D3Q19}[lattice]
+    p.nx, p.ny = int(shape[0]), int(shape[1])
+    p.nz = int(shape[2]) if len(shape) > 2 else 1
+    p.precision = {"fp64": LB_FP64, "fp32": LB_FP32_SHIFTED}[precision]
+    p.tau, p.G = float(tau), float(G)
+    p.g_convention = {"literal": LB_G_LITERAL, "paper": LB_G_TIMES_CS2}[convention]
+    p.rho0_shift = float(rho0_shift)
+    return p
+
+
+def _groups_arrays(bases, weights, dim):
+    b = np.ascontiguousarray(np.asarray(bases, dtype=np.int32).reshape(-1, dim))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).ravel())
+    if len(b) != len(w):
+        raise ValueError("one weight per group")
+    return b, w
+
+
+def lb_expand_stencil(dim, bases, weights):
+    """(pair vectors [P][3], pair weights [P], lb_stencil_info)."""
+    b, w = _groups_arrays(bases, weights, dim)
+    vec = np.zeros((LB_MAX_PAIRS, 3), dtype=np.int32)
+    pw = np.zeros(LB_MAX_PAIRS)
+    n = ctypes.c_int(0)
+    info = lb_stencil_info()
+    _check(_lib.lb_expand_stencil(dim, len(w), b.ctypes.data_as(_ip), _ptr(w), LB_MAX_PAIRS,
+                                  vec.ctypes.data_as(_ip), _ptr(pw), ctypes.byref(n),
+                                  ctypes.byref(info)), "lb_expand_stencil")
+    return vec[:n.value].copy(), pw[:n.value].copy(), info
+
+
+def lb_create(params, rho_init, u_init=None, stream=None):
+    """Returns an opaque context handle (int).  rho_init: N float64 values
+    (x fastest); u_init: [D][N] or None; stream: cudaStream_t as int (e.g.
+    ``torch.cuda.current_stream().cuda_stream``) or None."""
+    N = max(params.nx * params.ny * params.nz, 0)
+    rho = _f64(rho_init).ravel()
+    u = _f64(u_init).ravel() if u_init is not None else None
+    if rho.size < N:
+        raise ValueError(f"rho_init has {rho.size} values, the lattice {N}")
+    ctx = _vp()
+    _check(_lib.lb_create(ctypes.byref(params), _ptr(rho), _ptr(u),
+                          _vp(stream) if stream else None, ctypes.byref(ctx)), "lb_create")
+    return ctx.value
+
+
+def lb_destroy(ctx):
+    _check(_lib.lb_destroy(_vp(ctx)), "lb_destroy")
+
+
+def lb_set_stencil(ctx, dim, bases, weights):
+    b, w = _groups_arrays(bases, weights, dim)
+    info = lb_stencil_info()
+    _check(_lib.lb_set_stencil(_vp(ctx), len(w), b.ctypes.data_as(_ip), _ptr(w),
+                               ctypes.byref(info)), "lb_set_stencil")
+    return info
+
+
+def lb_step(ctx, nsteps=1):
+    _check(_lib.lb_step(_vp(ctx), int(nsteps)), "lb_step")
+
+
+def lb_sync(ctx):
+    """Returns the status (LB_OK or LB_EUNSTABLE); raises for other errors."""
+    s = _lib.lb_sync(_vp(ctx))
+    if s not in (LB_OK, LB_EUNSTABLE):
+        raise LbError(s, "lb_sync")
+    return s
+
+
+def lb_observables(ctx):
+    """dict of observables; 'status' is LB_OK or LB_EUNSTABLE."""
+    o = lb_obs()
+    s = _lib.lb_observables(_vp(ctx), ctypes.byref(o))
+    if s not in (LB_OK, LB_EUNSTABLE):
+        raise LbError(s, "lb_observables")
+    return {"mass": o.mass, "mom": list(o.mom), "umax": o.umax, "rho_min": o.rho_min,
+            "rho_max": o.rho_max, "step": o.step, "error_step": o.error_step,
+            "exp_ambiguous": o.exp_ambiguous, "status": s}
+
+
+def lb_pressure_tensor(ctx, N, dim, out=None):
+    nc = 3 if dim == 2 else 6
+    out = np.empty((nc, N)) if out is None else out
+    _check(_lib.lb_pressure_tensor(_vp(ctx), _ptr(out)), "lb_pressure_tensor")
+    return out
+
+
+def lb_get_fields(ctx, N, dim):
+    rho = np.empty(N)
+    u = np.empty((dim, N))
+    _check(_lib.lb_get_fields(_vp(ctx), _ptr(rho), _ptr(u)), "lb_get_fields")
+    return rho, u
+
+
+def lb_get_state(ctx, Q, N, out=None):
+    f = np.empty((Q, N)) if out is None else out
+    _check(_lib.lb_get_state(_vp(ctx), _ptr(f)), "lb_get_state")
+    return f
+
+
+def lb_set_state(ctx, f):
+    f = _f64(f)
+    _check(_lib.lb_set_state(_vp(ctx), _ptr(f)), "lb_set_state")
+
+
+def lb_exp_cr(x):
+    x = _f64(x).ravel()
+    y = np.empty_like(x)
+    amb = ctypes.c_longlong(0)
+    _check(_lib.lb_exp_cr(_ptr(x), _ptr(y), len(x), ctypes.byref(amb)), "lb_exp_cr")
+    return y, amb.value
+
+
+def lb_kernel_launches(ctx):
+    return int(_lib.lb_kernel_launches(_vp(ctx)))
+
+
+LB_KERNEL_PSI, LB_KERNEL_COLLIDE, LB_KERNEL_FUSED, LB_KERNEL_OTHER = range(4)
+KERNEL_KINDS = ("psi", "collide", "fused", "other")
+
+
+def lb_timing(ctx, enable):
+    _check(_lib.lb_timing(_vp(ctx), int(bool(enable))), "lb_timing")
+
+
+def lb_timing_read(ctx):
+    """{kind: (milliseconds, launches)} of the kernels timed since lb_timing(1)."""
+    ms = np.zeros(4)
+    n = (ctypes.c_longlong * 4)()
+    _check(_lib.lb_timing_read(_vp(ctx), _ptr(ms), n), "lb_timing_read")
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+class Lattice:
+    """Owner of one context: ``Lattice('D3Q19', (nx, ny, nz), rho, ...)``.
+    Arrays in and out are numpy with shape (nz, ny, nx) / (C, nz, ny, nx)."""
+
+    def __init__(self, lattice, shape_xyz, rho, stencil_bases=None, stencil_weights=None,
+                 precision="fp64", tau=1.0, G=-5.0, convention="literal", rho0_shift=1.0,
+                 u=None, stream=None):
+        self.params = make_params(lattice, shape_xyz, precision, tau, G, convention, rho0_shift)
+        self.D = 2 if lattice == "D2Q9" else 3
+        self.Q = 9 if lattice == "D2Q9" else 19
+        p = self.params
+        self.shape = (p.nz, p.ny, p.nx)
+        self.N = p.nx * p.ny * p.nz
+        self.ctx = lb_create(p, rho, u, stream)
+        self.info = None
+        if stencil_bases is not None:
+            self.set_stencil(stencil_bases, stencil_weights)
+
+    def set_stencil(self, bases, weights):
+        self.info = lb_set_stencil(self.ctx, self.D, bases, weights)
+        return self.info
+
+    def step(self, n=1):
+        lb_step(self.ctx, n)
+
+    def sync(self):
+        return lb_sync(self.ctx)
+
+    def observables(self):
+        return lb_observables(self.ctx)
+
+    def pressure_tensor(self):
+        return lb_pressure_tensor(self.ctx, self.N, self.D).reshape((-1,) + self.shape)
+
+    def fields(self):
+        rho, u = lb_get_fields(self.ctx, self.N, self.D)
+        return rho.reshape(self.shape), u.reshape((self.D,) + self.shape)
+
+    def state(self):
+        return lb_get_state(self.ctx, self.Q, self.N).reshape((self.Q,) + self.shape)
+
+    def set_state(self, f):
+        lb_set_state(self.ctx, np.asarray(f).reshape(self.Q, self.N))
+
+    def launches(self):
+        return lb_kernel_launches(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

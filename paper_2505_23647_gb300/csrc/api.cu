@@ -1,0 +1,579 @@
+// api.cu -- host implementation of the C ABI declared in include/sclbm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace sclbm;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+lb_status cuda_fail(cudaError_t e, const char *where) {
+    std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", where, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return LB_ENOMEM;
+    if (e == cudaErrorNotSupported) return LB_EUNSUPPORTED;
+    return LB_ECUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+// ---- stencil expansion (canonical pair order, see sclbm.h) ----------------
+struct Group {
+    std::array<int, 3> cb;  // sorted absolute components, descending
+    double w;
+};
+
+bool lex_greater(const std::array<int, 3> &a, const std::array<int, 3> &b) {
+    for (int k = 0; k < 3; ++k)
+        if (a[k] != b[k]) return a[k] > b[k];
+    return false;
+}
+
+// orbit of a base under permutations and sign flips (dim components)
+std::vector<std::array<int, 3>> orbit(const std::array<int, 3> &cb, int dim) {
+    std::vector<std::array<int, 3>> out;
+    int perm[3] = {0, 1, 2};
+    std::vector<int> idx(perm, perm + dim);
+    std::sort(idx.begin(), idx.end());
+    do {
+        for (int s = 0; s < (1 << dim); ++s) {
+            std::array<int, 3> v = {0, 0, 0};
+            for (int k = 0; k < dim; ++k) {
+                int c = cb[idx[k]];
+                v[k] = (s >> k & 1) ? -c : c;
+            }
+            if (v[0] == 0 && v[1] == 0 && v[2] == 0) continue;
+            if (std::find(out.begin(), out.end(), v) == out.end()) out.push_back(v);
+        }
+    } while (std::next_permutation(idx.begin(), idx.end()));
+    return out;
+}
+
+bool is_rep(const std::array<int, 3> &v) {
+    for (int k = 0; k < 3; ++k)
+        if (v[k]) return v[k] > 0;
+    return false;
+}
+
+double dfact(int k) {
+    double r = 1;
+    while (k > 1) { r *= k; k -= 2; }
+    return r;
+}
+
+// Delta^{idx}: number of pairings of equal indices (zero if a count is odd).
+double iso_tensor(const int *cnt) {
+    double v = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (cnt[k] % 2) return 0;
+        v *= dfact(cnt[k] - 1);
+    }
+    return v;
+}
+
+lb_status expand(int dim, int n_groups, const int *base, const double *W,
+                 std::vector<std::array<int, 3>> &vec, std::vector<double> &w,
+                 std::vector<std::array<int, 3>> &gbase, std::vector<double> &gw,
+                 lb_stencil_info *info) {
+    if ((dim != 2 && dim != 3) || n_groups < 1 || !base || !W) return LB_EINVAL;
+    std::vector<Group> gs;
+    for (int g = 0; g < n_groups; ++g) {
+        std::array<int, 3> a = {0, 0, 0};
+        for (int k = 0; k < dim; ++k) {
+            int c = base[g * dim + k];
+            if (c < -LB_MAX_RADIUS || c > LB_MAX_RADIUS) return LB_EINVAL;
+            a[k] = c < 0 ? -c : c;
+        }
+        std::sort(a.begin(), a.end(), [](int p, int q) { return p > q; });
+        if (a[0] == 0) return LB_EINVAL;
+        if (!std::isfinite(W[g])) return LB_EINVAL;
+        for (auto &o : gs)
+            if (o.cb == a) return LB_EINVAL;
+        gs.push_back({a, W[g]});
+    }
+    std::stable_sort(gs.begin(), gs.end(), [](const Group &p, const Group &q) {
+        int sp = p.cb[0] * p.cb[0] + p.cb[1] * p.cb[1] + p.cb[2] * p.cb[2];
+        int sq = q.cb[0] * q.cb[0] + q.cb[1] * q.cb[1] + q.cb[2] * q.cb[2];
+        if (sp != sq) return sp < sq;
+        return lex_greater(p.cb, q.cb);
+    });
+    vec.clear();
+    w.clear();
+    gbase.clear();
+    gw.clear();
+    int radius = 0;
+    for (auto &g : gs) {
+        auto orb = orbit(g.cb, dim);
+        std::vector<std::array<int, 3>> reps;
+        for (auto &v : orb)
+            if (is_rep(v)) reps.push_back(v);
+        std::sort(reps.begin(), reps.end(), lex_greater);
+        for (auto &v : reps) {
+            vec.push_back(v);
+            w.push_back(g.w);
+        }
+        gbase.push_back(g.cb);
+        gw.push_back(g.w);
+        radius = std::max(radius, g.cb[0]);
+    }
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->n_groups = n_groups;
+        info->n_pairs = (int)vec.size();
+        info->n_vectors = 2 * (int)vec.size();
+        info->radius = radius;
+        auto mom = [&](int px, int py, int pz) {
+            double s = 0;
+            for (size_t a = 0; a < vec.size(); ++a) {
+                double t = 2.0 * w[a];  // e and -e (even powers)
+                for (int k = 0; k < px; ++k) t *= vec[a][0];
+                for (int k = 0; k < py; ++k) t *= vec[a][1];
+                for (int k = 0; k < pz; ++k) t *= vec[a][2];
+                s += t;
+            }
+            return s;
+        };
+        info->e2 = mom(2, 0, 0);
+        info->e4 = mom(2, 2, 0);
+        info->e6 = mom(4, 2, 0) / 3.0;
+        info->e8 = mom(4, 4, 0) / 9.0;
+        for (int oi = 0; oi < 4; ++oi) {
+            const int order = 4 + 2 * oi;
+            // balanced reference tuple x^{2a} y^{2b}
+            int a2 = ((order / 2 + 1) / 2) * 2, b2 = order - a2;
+            int rc[3] = {a2, b2, 0};
+            const double eref = mom(a2, b2, 0) / iso_tensor(rc);
+            double worst = 0;
+            for (int px = order; px >= 0; --px)
+                for (int py = order - px; py >= 0; --py) {
+                    int pz = order - px - py;
+                    if (dim == 2 && pz) continue;
+                    int cnt[3] = {px, py, pz};
+                    double m = mom(px, py, pz);
+                    double d = iso_tensor(cnt);
+                    worst = std::max(worst, std::fabs(m - eref * d));
+                }
+            info->iso_residual[oi] = worst;
+        }
+    }
+    return LB_OK;
+}
+
+void set_consts(lb_ctx *c) {
+    double w[19];
+    if (c->Q == 9) {
+        w[0] = 4.0 / 9.0;
+        for (int i = 1; i <= 4; ++i) w[i] = 1.0 / 9.0;
+        for (int i = 5; i <= 8; ++i) w[i] = 1.0 / 36.0;
+    } else {
+        w[0] = 1.0 / 3.0;
+        for (int i = 1; i <= 6; ++i) w[i] = 1.0 / 18.0;
+        for (int i = 7; i <= 18; ++i) w[i] = 1.0 / 36.0;
+    }
+    const double tau = c->p.tau;
+    c->k.omega = 1.0 / tau;
+    const double pref = 1.0 - 1.0 / (2.0 * tau);
+    for (int i = 0; i < 19; ++i) {
+        c->k.w[i] = i < c->Q ? w[i] : 0.0;
+        c->k.cw[i] = i < c->Q ? pref * w[i] : 0.0;
+    }
+    c->Gp = c->p.g_convention == LB_G_TIMES_CS2 ? c->p.G / 3.0 : c->p.G;
+    c->k.mGp = -c->Gp;
+    c->k.rho0 = c->p.rho0_shift;
+}
+
+size_t tsize(const lb_ctx *c) { return c->p.precision == LB_FP64 ? 8 : 4; }
+
+lb_status ensure_scratch(lb_ctx *c, size_t bytes) {
+    if (c->dscratch_bytes >= bytes) return LB_OK;
+    if (c->dscratch) {
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaFree(c->dscratch));
+        c->dscratch = nullptr;
+        c->dscratch_bytes = 0;
+    }
+    CK(cudaMalloc(&c->dscratch, bytes));
+    c->dscratch_bytes = bytes;
+    return LB_OK;
+}
+
+lb_status check_flags(lb_ctx *c, Flags *h) {
+    CK(cudaMemcpyAsync(h, c->flags, sizeof(Flags), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return h->err_step != ULLONG_MAX ? LB_EUNSTABLE : LB_OK;
+}
+
+}  // namespace
+
+namespace sclbm {
+
+void tm_begin(lb_ctx *c, int kind) {
+    if (!c->timing) return;
+    if (c->ev_used + 2 > c->ev_cap) {
+        int cap = c->ev_cap ? 2 * c->ev_cap : 256;
+        cudaEvent_t *ev = (cudaEvent_t *)std::realloc(c->ev, cap * sizeof(cudaEvent_t));
+        int *kd = (int *)std::realloc(c->ev_kind, (cap / 2) * sizeof(int));
+        if (!ev || !kd) {  // out of host memory: stop timing, keep stepping
+            if (ev) c->ev = ev;
+            if (kd) c->ev_kind = kd;
+            c->timing = false;
+            return;
+        }
+        c->ev = ev;
+        c->ev_kind = kd;
+        for (int i = c->ev_cap; i < cap; ++i) cudaEventCreate(&c->ev[i]);
+        c->ev_cap = cap;
+    }
+    c->ev_kind[c->ev_used / 2] = kind;
+    cudaEventRecord(c->ev[c->ev_used], c->stream);
+}
+
+void tm_end(lb_ctx *c) {
+    if (!c->timing) return;
+    cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+    c->ev_used += 2;
+}
+
+}  // namespace sclbm
+
+extern "C" {
+
+lb_status lb_timing(lb_ctx *c, int enable) {
+    if (!c) return LB_EINVAL;
+    if (enable) {
+        CK(cudaStreamSynchronize(c->stream));
+        c->ev_used = 0;
+        for (int k = 0; k < LB_KERNEL_KINDS; ++k) {
+            c->kind_ms[k] = 0.0;
+            c->kind_n[k] = 0;
+        }
+    }
+    c->timing = enable != 0;
+    return LB_OK;
+}
+
+lb_status lb_timing_read(lb_ctx *c, double *ms, long long *launches) {
+    if (!c) return LB_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int e = 0; e < c->ev_used; e += 2) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev[e], c->ev[e + 1]));
+        c->kind_ms[c->ev_kind[e / 2]] += t;
+        c->kind_n[c->ev_kind[e / 2]] += 1;
+    }
+    c->ev_used = 0;
+    for (int k = 0; k < LB_KERNEL_KINDS; ++k) {
+        if (ms) ms[k] = c->kind_ms[k];
+        if (launches) launches[k] = c->kind_n[k];
+    }
+    return LB_OK;
+}
+
+
+const char *lb_status_str(lb_status s) {
+    switch (s) {
+        case LB_OK: return "LB_OK";
+        case LB_EINVAL: return "LB_EINVAL: invalid argument";
+        case LB_ENOMEM: return "LB_ENOMEM: out of memory";
+        case LB_ECUDA: return "LB_ECUDA: CUDA runtime error";
+        case LB_EUNSTABLE: return "LB_EUNSTABLE: density check failed (n <= 0 or NaN)";
+        case LB_EUNSUPPORTED: return "LB_EUNSUPPORTED: not covered by this build";
+        case LB_ESTATE: return "LB_ESTATE: call out of order";
+    }
+    return "unknown lb_status";
+}
+
+const char *lb_last_cuda_error(void) { return g_cuda_err; }
+
+lb_status lb_params_default(lb_params *p) {
+    if (!p) return LB_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->lattice = LB_D2Q9;
+    p->nx = 64;
+    p->ny = 64;
+    p->nz = 1;
+    p->precision = LB_FP64;
+    p->tau = 1.0;
+    p->G = -5.0;
+    p->g_convention = LB_G_LITERAL;
+    p->psi_kind = LB_PSI_EXP;
+    p->psi_eps = 0.0;
+    p->rho0_shift = 1.0;
+    return LB_OK;
+}
+
+lb_status lb_expand_stencil(int dim, int n_groups, const int *base_vectors, const double *W,
+                            int max_pairs, int *pair_vec, double *pair_w, int *n_pairs,
+                            lb_stencil_info *info) {
+    std::vector<std::array<int, 3>> vec, gb;
+    std::vector<double> w, gw;
+    lb_status s = expand(dim, n_groups, base_vectors, W, vec, w, gb, gw, info);
+    if (s != LB_OK) return s;
+    if ((int)vec.size() > max_pairs && (pair_vec || pair_w)) return LB_EINVAL;
+    if (n_pairs) *n_pairs = (int)vec.size();
+    for (size_t a = 0; a < vec.size() && (int)a < max_pairs; ++a) {
+        if (pair_vec)
+            for (int k = 0; k < 3; ++k) pair_vec[3 * a + k] = vec[a][k];
+        if (pair_w) pair_w[a] = w[a];
+    }
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_init,
+                    void *cuda_stream, lb_ctx **out) {
+    if (!p || !rho_init || !out) return LB_EINVAL;
+    *out = nullptr;
+    if (p->lattice != LB_D2Q9 && p->lattice != LB_D3Q19) return LB_EINVAL;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return LB_EINVAL;
+    if (p->lattice == LB_D2Q9 && p->nz != 1) return LB_EINVAL;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED) return LB_EINVAL;
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau) || !std::isfinite(p->G)) return LB_EINVAL;
+    if (p->g_convention != LB_G_LITERAL && p->g_convention != LB_G_TIMES_CS2) return LB_EINVAL;
+    if (p->psi_kind != LB_PSI_EXP) return LB_EUNSUPPORTED;
+    if (!std::isfinite(p->rho0_shift)) return LB_EINVAL;
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    for (long long s = 0; s < N; ++s)
+        if (!(rho_init[s] > 0.0) || !std::isfinite(rho_init[s])) return LB_EINVAL;
+
+    lb_ctx *c = new (std::nothrow) lb_ctx();
+    if (!c) return LB_ENOMEM;
+    c->p = *p;
+    c->D = p->lattice == LB_D2Q9 ? 2 : 3;
+    c->Q = p->lattice == LB_D2Q9 ? 9 : 19;
+    c->g = {p->nx, p->ny, p->nz, N};
+    set_consts(c);
+    c->cur = 0;
+    auto fail = [&](lb_status s) {
+        lb_destroy(c);
+        return s;
+    };
+    cudaError_t e;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+        c->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
+        c->own_stream = true;
+    }
+    const size_t fbytes = (size_t)c->Q * N * tsize(c);
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&c->f[b], fbytes);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(f)"));
+    }
+    e = cudaMalloc(&c->psi, (size_t)N * tsize(c));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(psi)"));
+    e = cudaMalloc(&c->flags, sizeof(Flags));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(flags)"));
+    e = cudaMalloc(&c->red, 1024 * 128);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(red)"));
+    Flags h0 = {ULLONG_MAX, 0, 0, 0};
+    e = cudaMemcpyAsync(c->flags, &h0, sizeof h0, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(flags)"));
+    lb_status s = ensure_scratch(c, (size_t)(1 + c->D) * N * sizeof(double));
+    if (s != LB_OK) return fail(s);
+    double *rho_d = c->dscratch, *u_d = u_init ? c->dscratch + N : nullptr;
+    e = cudaMemcpyAsync(rho_d, rho_init, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(rho)"));
+    if (u_init) {
+        e = cudaMemcpyAsync(u_d, u_init, c->D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(u)"));
+    }
+    e = p->precision == LB_FP64 ? f64_init(c, rho_d, u_d) : f32_init(c, rho_d, u_d);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "init kernel"));
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "lb_create sync"));
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx *c) {
+    if (!c) return LB_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_valid) cudaGraphExecDestroy(c->graph);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->psi);
+    cudaFree(c->dscratch);
+    cudaFree(c->red);
+    cudaFree(c->flags);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    for (int i = 0; i < c->ev_cap; ++i) cudaEventDestroy(c->ev[i]);
+    std::free(c->ev);
+    std::free(c->ev_kind);
+    delete c;
+    return LB_OK;
+}
+
+lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const double *W,
+                         lb_stencil_info *info) {
+    if (!c) return LB_EINVAL;
+    std::vector<std::array<int, 3>> vec, gb;
+    std::vector<double> w, gw;
+    lb_stencil_info tmp;
+    lb_status s = expand(c->D, n_groups, base_vectors, W, vec, w, gb, gw, &tmp);
+    if (s != LB_OK) return s;
+    if ((int)vec.size() > MAXP) return LB_EINVAL;
+    c->pairs64.npairs = c->pairs32.npairs = (int)vec.size();
+    c->pairs64.radius = c->pairs32.radius = tmp.radius;
+    for (size_t a = 0; a < vec.size(); ++a) {
+        for (int k = 0; k < 3; ++k) {
+            c->pairs64.v[a][k] = (signed char)vec[a][k];
+            c->pairs32.v[a][k] = (signed char)vec[a][k];
+        }
+        c->pairs64.w[a] = w[a];
+        c->pairs32.w[a] = (float)w[a];
+    }
+    c->n_groups = (int)gb.size();
+    for (size_t g = 0; g < gb.size(); ++g) {
+        for (int k = 0; k < 3; ++k) c->group_base[g][k] = gb[g][k];
+        c->group_w[g] = gw[g];
+    }
+    c->stencil_set = true;
+    if (c->graph_valid) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph_valid = false;
+    }
+    if (info) *info = tmp;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx *c, int nsteps) {
+    if (!c || nsteps < 0) return LB_EINVAL;
+    if (!c->stencil_set) return LB_ESTATE;
+    for (int t = 0; t < nsteps; ++t) {
+        cudaError_t e = c->p.precision == LB_FP64 ? f64_step(c) : f32_step(c);
+        if (e != cudaSuccess) return cuda_fail(e, "step kernels");
+    }
+    c->steps += nsteps;
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx *c) {
+    if (!c) return LB_EINVAL;
+    Flags h;
+    return check_flags(c, &h);
+}
+
+lb_status lb_observables(lb_ctx *c, lb_obs *out) {
+    if (!c || !out) return LB_EINVAL;
+    if (!c->stencil_set) return LB_ESTATE;
+    const long long N = c->g.N;
+    lb_status s = ensure_scratch(c, (size_t)(2 + 2 * c->D) * N * sizeof(double) + 16 * sizeof(double));
+    if (s != LB_OK) return s;
+    double *n = c->dscratch, *u = n + 2 * N, *mom = u + c->D * N, *res = mom + c->D * N;
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_fields(c, n, u, mom) : f32_fields(c, n, u, mom);
+    if (e != cudaSuccess) return cuda_fail(e, "fields kernels");
+    e = obs_reduce(c, n, u, mom, res);
+    if (e != cudaSuccess) return cuda_fail(e, "reduction kernels");
+    double h[7];
+    CK(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    Flags f;
+    lb_status st = check_flags(c, &f);
+    if (st != LB_OK && st != LB_EUNSTABLE) return st;
+    out->mass = h[0];
+    for (int k = 0; k < 3; ++k) out->mom[k] = k < c->D ? h[1 + k] : 0.0;
+    out->umax = h[4];
+    out->rho_min = h[5];
+    out->rho_max = h[6];
+    out->step = c->steps;
+    out->error_step = f.err_step == ULLONG_MAX ? -1 : (long long)f.err_step;
+    out->exp_ambiguous = (long long)f.exp_amb;
+    return st;
+}
+
+lb_status lb_pressure_tensor(lb_ctx *c, double *out) {
+    if (!c || !out) return LB_EINVAL;
+    if (!c->stencil_set) return LB_ESTATE;
+    const long long N = c->g.N;
+    const int nc = c->D == 2 ? 3 : 6;
+    lb_status s = ensure_scratch(c, (size_t)(2 + nc) * N * sizeof(double));
+    if (s != LB_OK) return s;
+    double *n = c->dscratch, *psi = n + N, *P = psi + N;
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_density_psi(c, n, psi) : f32_density_psi(c, n, psi);
+    if (e != cudaSuccess) return cuda_fail(e, "density kernel");
+    e = ptensor(c, n, psi, P);
+    if (e == cudaErrorNotSupported) return LB_EUNSUPPORTED;
+    if (e != cudaSuccess) return cuda_fail(e, "pressure tensor kernel");
+    CK(cudaMemcpyAsync(out, P, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_fields(lb_ctx *c, double *rho, double *u) {
+    if (!c) return LB_EINVAL;
+    if (!c->stencil_set) return LB_ESTATE;
+    const long long N = c->g.N;
+    lb_status s = ensure_scratch(c, (size_t)(2 + 2 * c->D) * N * sizeof(double));
+    if (s != LB_OK) return s;
+    double *n = c->dscratch, *ud = n + 2 * N, *mom = ud + c->D * N;
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_fields(c, n, ud, mom) : f32_fields(c, n, ud, mom);
+    if (e != cudaSuccess) return cuda_fail(e, "fields kernels");
+    if (rho) CK(cudaMemcpyAsync(rho, n, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (u) CK(cudaMemcpyAsync(u, ud, c->D * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_state(lb_ctx *c, double *f) {
+    if (!c || !f) return LB_EINVAL;
+    const long long N = c->g.N;
+    lb_status s = ensure_scratch(c, (size_t)c->Q * N * sizeof(double));
+    if (s != LB_OK) return s;
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, c->dscratch) : f32_get_state(c, c->dscratch);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state kernel");
+    CK(cudaMemcpyAsync(f, c->dscratch, (size_t)c->Q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_set_state(lb_ctx *c, const double *f) {
+    if (!c || !f) return LB_EINVAL;
+    const long long N = c->g.N;
+    lb_status s = ensure_scratch(c, (size_t)c->Q * N * sizeof(double));
+    if (s != LB_OK) return s;
+    CK(cudaMemcpyAsync(c->dscratch, f, (size_t)c->Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_set_state(c, c->dscratch) : f32_set_state(c, c->dscratch);
+    if (e != cudaSuccess) return cuda_fail(e, "set_state kernel");
+    CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_exp_cr(const double *x, double *y, long long n, long long *n_ambiguous) {
+    if (n < 0 || (n > 0 && (!x || !y))) return LB_EINVAL;
+    if (n_ambiguous) *n_ambiguous = 0;
+    if (n == 0) return LB_OK;
+    double *d = nullptr;
+    unsigned long long *amb = nullptr;
+    CK(cudaMalloc(&d, 2 * n * sizeof(double) + 16));
+    amb = (unsigned long long *)(d + 2 * n);
+    cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(amb, 0, sizeof *amb);
+    if (e == cudaSuccess) e = exp_batch(d, d + n, n, amb, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, amb, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_exp_cr");
+    if (n_ambiguous) *n_ambiguous = (long long)h;
+    return LB_OK;
+}
+
+long long lb_kernel_launches(const lb_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// internal.h -- context layout and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sclbm.h"
+
+namespace sclbm {
+
+constexpr int MAXP = LB_MAX_PAIRS;
+
+// Canonical (e,-e) pairs of the forcing stencil, passed by value to kernels
+// (kernel parameters live in the constant bank, so every thread of a warp
+// reading the same pair is a broadcast).
+struct PairsF64 {
+    int npairs;
+    int radius;
+    signed char v[MAXP][3];
+    double w[MAXP];
+};
+struct PairsF32 {
+    int npairs;
+    int radius;
+    signed char v[MAXP][3];
+    float w[MAXP];
+};
+
+// Per-context constants of the collision (formed on the host once, in the
+// same expressions as the reference: omega = 1/tau, cw_i = (1 - 1/(2 tau)) w_i).
+struct Consts {
+    double w[19];
+    double cw[19];
+    double omega;
+    double mGp;     // -G'
+    double rho0;    // FP32 shift
+};
+
+struct Geom {
+    int nx, ny, nz;
+    long long N;
+};
+
+// Device-side counters of a context.
+struct Flags {
+    unsigned long long err_step;   // first failing step (ULLONG_MAX: none)
+    unsigned long long step;       // steps completed on the device
+    unsigned long long exp_amb;    // uncertified exp roundings
+    unsigned long long pad;
+};
+
+}  // namespace sclbm
+
+struct lb_ctx {
+    lb_params p;
+    int D, Q;
+    sclbm::Geom g;
+    double Gp;
+    sclbm::Consts k;
+    sclbm::PairsF64 pairs64;
+    sclbm::PairsF32 pairs32;
+    int n_groups;
+    int group_base[LB_MAX_PAIRS][3];
+    double group_w[LB_MAX_PAIRS];
+    bool stencil_set;
+    bool fast3d_ok;           // the fused FP32 D3Q19 path applies
+    void *f[2];               // population buffers [Q][N] (post-collision, pre-stream)
+    int cur;                  // buffer holding the current state
+    void *psi;                // [N] psi of the precision in use
+    double *dscratch;         // on-demand binary64 scratch
+    size_t dscratch_bytes;
+    double *red;              // reduction partials
+    sclbm::Flags *flags;      // device counters
+    cudaStream_t stream;
+    bool own_stream;
+    cudaGraphExec_t graph;    // two steps, captured on first use
+    bool graph_valid;
+    long long steps;          // host-side step count
+    long long launches;       // kernels launched
+    // per-kernel timing (lb_timing)
+    bool timing;
+    cudaEvent_t *ev;          // event pool
+    int ev_cap, ev_used;
+    int *ev_kind;             // kind of each (start, stop) pair
+    double kind_ms[LB_KERNEL_KINDS];
+    long long kind_n[LB_KERNEL_KINDS];
+};
+
+namespace sclbm {
+// per-kernel timing brackets (no-ops unless lb_timing is enabled)
+void tm_begin(lb_ctx *c, int kind);
+void tm_end(lb_ctx *c);
+// precision-specific launchers (fp64.cu / fp32.cu)
+cudaError_t f64_init(lb_ctx *c, const double *rho, const double *u);
+cudaError_t f64_step(lb_ctx *c);          // one step, swaps buffers
+cudaError_t f64_psi(lb_ctx *c);           // psi of current state into c->psi
+cudaError_t f64_fields(lb_ctx *c, double *n, double *u, double *mom);
+cudaError_t f64_get_state(lb_ctx *c, double *f);
+cudaError_t f64_set_state(lb_ctx *c, const double *f);
+cudaError_t f64_density_psi(lb_ctx *c, double *n, double *psi);
+cudaError_t f32_init(lb_ctx *c, const double *rho, const double *u);
+cudaError_t f32_step(lb_ctx *c);
+cudaError_t f32_psi(lb_ctx *c);
+cudaError_t f32_fields(lb_ctx *c, double *n, double *u, double *mom);
+cudaError_t f32_get_state(lb_ctx *c, double *f);
+cudaError_t f32_set_state(lb_ctx *c, const double *f);
+cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi);
+// precision-independent (fp64.cu): reductions, pressure tensor, exp diagnostic
+cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
+                       double *out_host9);
+cudaError_t ptensor(lb_ctx *c, const double *n, const double *psi, double *out);
+cudaError_t exp_batch(const double *x, double *y, long long n,
+                      unsigned long long *amb, cudaStream_t s);
+}  // namespace sclbm

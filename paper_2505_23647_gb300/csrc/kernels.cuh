@@ -1,0 +1,355 @@
+// kernels.cuh -- per-node kernels of the Shan-Chen step, templated on the
+// storage/compute type T (double or float), lattice (D, Q) and the FP32
+// population shift.  Included by fp64.cu (built with -fmad=false so binary64
+// expressions round exactly as written) and fp32.cu.
+//
+// State layout: two population buffers A, B of [Q][N] T (structure of
+// arrays, x fastest).  A holds post-collision, pre-streaming populations of
+// the previous step, so the population f_i(x) at the current time is
+// A_i(x - xi_i) ("pull" streaming, eq. lbm).  One step is
+//   k_psi:     n(x) = sum_i A_i(x - xi_i), psi(x)   -> psi[N]
+//   k_collide: pull f_i(x), force from psi (eq. sc_f), BGK + Guo -> B_i(x)
+// and the buffers swap.
+#pragma once
+#include <cuda_runtime.h>
+#include <limits.h>
+
+#include "expcr.cuh"
+#include "internal.h"
+
+namespace sclbm {
+
+// Velocity tables in the state layout's order (see sclbm.h).
+template <int Q>
+__host__ __device__ constexpr int cvel(int i, int mu);
+template <>
+__host__ __device__ constexpr int cvel<9>(int i, int mu) {
+    constexpr signed char t[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                     {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+    return t[i][mu];
+}
+template <>
+__host__ __device__ constexpr int cvel<19>(int i, int mu) {
+    constexpr signed char t[19][3] = {
+        {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+        {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
+        {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][mu];
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ long long site(const Geom &g, int x, int y, int z) {
+    return ((long long)wrapi(z, g.nz) * g.ny + wrapi(y, g.ny)) * g.nx + wrapi(x, g.nx);
+}
+
+__device__ __forceinline__ void coords(const Geom &g, long long s, int &x, int &y, int &z) {
+    long long q = s / g.nx;
+    x = (int)(s - q * g.nx);
+    z = (int)(q / g.ny);
+    y = (int)(q - (long long)z * g.ny);
+}
+
+template <typename T>
+struct ConstsT {
+    T w[19], cw[19], omega, mGp, rho0;
+};
+
+template <typename T>
+__device__ __forceinline__ T psi_of(T n, unsigned long long *amb);
+template <>
+__device__ __forceinline__ double psi_of<double>(double n, unsigned long long *amb) {
+    return exp_cr(-1.0 / n, amb);
+}
+template <>
+__device__ __forceinline__ float psi_of<float>(float n, unsigned long long *) {
+    return expf(-1.0f / n);
+}
+
+// Sum over a velocity's non-zero components, x then y then z: equal in value
+// to (c_x*a_x + c_y*a_y) + c_z*a_z with c in {-1,0,1} (terms with c = 0 add
+// a signed zero, which never changes a non-zero sum).
+template <int Q, int D, typename T>
+__device__ __forceinline__ T cdot(int i, const T *a) {
+    T r = T(0);
+    bool first = true;
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+        const int c = cvel<Q>(i, mu);
+        if (c == 0) continue;
+        if (first) {
+            r = c > 0 ? a[mu] : -a[mu];
+            first = false;
+        } else {
+            r = c > 0 ? r + a[mu] : r - a[mu];
+        }
+    }
+    return r;
+}
+
+template <typename T, int D, int Q>
+__device__ __forceinline__ void pull(const T *__restrict__ A, const Geom &g, int x, int y,
+                                     int z, T *fi) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        fi[i] = A[(long long)i * g.N +
+                  site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+}
+
+template <typename T, int Q>
+__device__ __forceinline__ T sum_q(const T *fi) {
+    T n = fi[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) n = n + fi[i];
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int D, int Q, bool SHIFT>
+__global__ void k_psi(const T *__restrict__ A, T *__restrict__ psi, Geom g, T rho0,
+                      Flags *flags) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+        T fi[Q];
+        pull<T, D, Q>(A, g, x, y, z, fi);
+        T n = sum_q<T, Q>(fi);
+        if (SHIFT) n = n + rho0;
+        if (!(n > T(0))) atomicMin(&flags->err_step, flags->step);
+        psi[s] = psi_of<T>(n, &flags->exp_amb);
+    }
+}
+
+template <typename T, typename PairsT, int D>
+__device__ __forceinline__ void force_acc(const T *__restrict__ psi, const Geom &g, int x, int y,
+                                          int z, const PairsT &P, T *acc) {
+    acc[0] = acc[1] = acc[2] = T(0);
+    for (int a = 0; a < P.npairs; ++a) {
+        const int e0 = P.v[a][0], e1 = P.v[a][1], e2 = P.v[a][2];
+        const T pp = psi[site(g, x + e0, y + e1, z + e2)];
+        const T pm = psi[site(g, x - e0, y - e1, z - e2)];
+        const T t = P.w[a] * (pp - pm);
+        const int e[3] = {e0, e1, e2};
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+            const int c = e[mu];
+            if (c == 1)
+                acc[mu] = acc[mu] + t;
+            else if (c == -1)
+                acc[mu] = acc[mu] - t;
+            else if (c != 0)
+                acc[mu] = acc[mu] + t * T(c);
+        }
+    }
+}
+
+// Moments, equilibrium and Guo source of one node; fi are pulled
+// populations (shifted in FP32 mode), n the density.  Writes post-collision
+// values to fo.  Returns u and j + F/2 if requested.
+template <typename T, int D, int Q, bool SHIFT>
+__device__ __forceinline__ void collide(const T *fi, T n, T dn, const T *F, const ConstsT<T> &k,
+                                        T *fo, T *uo, T *momo) {
+    T j[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+            const int c = cvel<Q>(i, mu);
+            if (c == 1) j[mu] = j[mu] + fi[i];
+            if (c == -1) j[mu] = j[mu] - fi[i];
+        }
+    T u[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+        const T m = j[mu] + T(0.5) * F[mu];
+        u[mu] = m / n;
+        if (momo) momo[mu] = m;
+        if (uo) uo[mu] = u[mu];
+    }
+    T uu = u[0] * u[0], uF = u[0] * F[0];
+#pragma unroll
+    for (int mu = 1; mu < D; ++mu) {
+        uu = uu + u[mu] * u[mu];
+        uF = uF + u[mu] * F[mu];
+    }
+    if (!fo) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T cu = cdot<Q, D, T>(i, u);
+        const T cF = cdot<Q, D, T>(i, F);
+        const T S = k.cw[i] * ((T(3) * cF + T(9) * (cu * cF)) - T(3) * uF);
+        if (SHIFT) {
+            const T geq = k.w[i] * (dn + n * ((T(3) * cu + T(4.5) * (cu * cu)) - T(1.5) * uu));
+            fo[i] = (fi[i] - k.omega * (fi[i] - geq)) + S;
+        } else {
+            const T feq = (k.w[i] * n) * (((T(1) + T(3) * cu) + T(4.5) * (cu * cu)) - T(1.5) * uu);
+            fo[i] = (fi[i] - k.omega * (fi[i] - feq)) + S;
+        }
+    }
+}
+
+template <typename T, typename PairsT, int D, int Q, bool SHIFT>
+__global__ void __launch_bounds__(256) k_collide(const T *__restrict__ A, T *__restrict__ B,
+                                                 const T *__restrict__ psi, Geom g,
+                                                 const PairsT P, const ConstsT<T> k,
+                                                 Flags *flags) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+        T fi[Q];
+        pull<T, D, Q>(A, g, x, y, z, fi);
+        T dn = sum_q<T, Q>(fi);
+        T n = SHIFT ? dn + k.rho0 : dn;
+        T acc[3];
+        force_acc<T, PairsT, D>(psi, g, x, y, z, P, acc);
+        const T pre = k.mGp * psi[s];
+        T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
+        T fo[Q];
+        collide<T, D, Q, SHIFT>(fi, n, dn, F, k, fo, nullptr, nullptr);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) B[(long long)i * g.N + s] = fo[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags->step = flags->step + 1;
+}
+
+// Density and psi in binary64 from a state of either precision.
+template <typename T, int D, int Q, bool SHIFT>
+__global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,
+                                double *__restrict__ n_out, double *__restrict__ psi_out,
+                                Flags *flags) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+        double fi[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            fi[i] = (double)A[(long long)i * g.N +
+                              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+        double n = sum_q<double, Q>(fi);
+        if (SHIFT) n = n + rho0;
+        n_out[s] = n;
+        psi_out[s] = exp_cr(-1.0 / n, &flags->exp_amb);
+    }
+}
+
+// n, u = (j + F/2)/n and j + F/2 in binary64 (state widened; FP64 states give
+// the step's exact values).
+template <typename T, int D, int Q, bool SHIFT>
+__global__ void k_fields64(const T *__restrict__ A, Geom g, const PairsF64 P, ConstsT<double> k,
+                           const double *__restrict__ n_in, const double *__restrict__ psi,
+                           double *__restrict__ u_out, double *__restrict__ mom_out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+        double fi[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            fi[i] = (double)A[(long long)i * g.N +
+                              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+        const double n = n_in[s];
+        double acc[3];
+        force_acc<double, PairsF64, D>(psi, g, x, y, z, P, acc);
+        const double pre = k.mGp * psi[s];
+        double F[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
+        double u[3], m[3];
+        collide<double, D, Q, false>(fi, n, n, F, k, nullptr, u, m);
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+            u_out[(long long)mu * g.N + s] = u[mu];
+            mom_out[(long long)mu * g.N + s] = m[mu];
+        }
+    }
+}
+
+// Equilibrium initial state: f_i(x) = f_eq(rho, u) stored at A_i(x - xi_i)
+// ... i.e. A_i(y) = f_i(y + xi_i).
+template <typename T, int D, int Q, bool SHIFT>
+__global__ void k_init(T *__restrict__ A, Geom g, const double *__restrict__ rho,
+                       const double *__restrict__ u, ConstsT<double> k) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+        double us[3] = {0.0, 0.0, 0.0};
+        if (u)
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) us[mu] = u[(long long)mu * g.N + s];
+        double uu = us[0] * us[0];
+#pragma unroll
+        for (int mu = 1; mu < D; ++mu) uu = uu + us[mu] * us[mu];
+        const double n = rho[s];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double cu = cdot<Q, D, double>(i, us);
+            double f = (k.w[i] * n) * (((1.0 + 3.0 * cu) + 4.5 * (cu * cu)) - 1.5 * uu);
+            if (SHIFT) f = f - k.w[i] * k.rho0;
+            A[(long long)i * g.N +
+              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)f;
+        }
+    }
+}
+
+template <typename T, int D, int Q, bool SHIFT>
+__global__ void k_get_state(const T *__restrict__ A, Geom g, double *__restrict__ out,
+                            ConstsT<double> k) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            double v = (double)A[(long long)i * g.N +
+                                 site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+            if (SHIFT) v = v + k.w[i] * k.rho0;
+            out[(long long)i * g.N + s] = v;
+        }
+    }
+}
+
+template <typename T, int D, int Q, bool SHIFT>
+__global__ void k_set_state(T *__restrict__ A, Geom g, const double *__restrict__ in,
+                            ConstsT<double> k) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            double v = in[(long long)i * g.N + s];
+            if (SHIFT) v = v - k.w[i] * k.rho0;
+            A[(long long)i * g.N +
+              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)v;
+        }
+    }
+}
+
+inline int grid_for(long long N, int block = 256, int cap = 152 * 32) {
+    long long b = (N + block - 1) / block;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <typename T>
+inline ConstsT<T> consts_as(const Consts &c) {
+    ConstsT<T> r;
+    for (int i = 0; i < 19; ++i) {
+        r.w[i] = (T)c.w[i];
+        r.cw[i] = (T)c.cw[i];
+    }
+    r.omega = (T)c.omega;
+    r.mGp = (T)c.mGp;
+    r.rho0 = (T)c.rho0;
+    return r;
+}
+
+}  // namespace sclbm

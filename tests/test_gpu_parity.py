@@ -1,0 +1,166 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+* binary64: populations bit for bit after up to 100 steps (D2Q9 and D3Q19,
+  E4/E8 and a radius-3 tuned stencil, tau = 1, 0.8, 1.3, both G
+  conventions, lattices that are not multiples of any block size);
+  fields, pressure tensor bit for bit; observables within one rounding of
+  the exact sums;
+* shifted binary32: density within 1e-5 relative after 100 steps;
+* the GPU exp is the correctly rounded one (bit for bit on 5e3 inputs,
+  subnormal results included);
+* the density check reports n <= 0 as LB_EUNSTABLE with its step.
+"""
+from fractions import Fraction as Fr
+from math import fsum
+
+import numpy as np
+import pytest
+
+import lbinputs as L
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2505_23647_gb300")
+
+
+def _run_pair(lattice, shape_xyz, stencil, rho, steps, precision="fp64", tau=1.0, G=-5.0,
+              convention="literal"):
+    lat = P.Lattice(lattice, shape_xyz, rho, stencil.bases, stencil.weights,
+                    precision=precision, tau=tau, G=G, convention=convention)
+    lat.step(steps)
+    assert lat.sync() == P.LB_OK
+    nx, ny = shape_xyz[0], shape_xyz[1]
+    nz = shape_xyz[2] if len(shape_xyz) > 2 else 1
+    o = oracle.Oracle(lattice, (nz, ny, nx), stencil.groups, tau=tau, G=G, convention=convention)
+    o.init_equilibrium(rho)
+    o.step(steps)
+    return lat, o
+
+
+T3_2D = L.stencil_e4e6_tuning_8(2, Fr(-2, 3), Fr(1, 10))
+
+FP64_CASES = [
+    # C1 shape: D2Q9 E4, 256 x 4 flat slab from the tanh profile, 100 steps
+    ("D2Q9", (256, 4), L.E4_2D, "slab", 100, 1.0, -5.0, "literal"),
+    ("D2Q9", (61, 47), L.E8_2D, "drop", 100, 0.8, -15.0, "paper"),
+    ("D2Q9", (40, 37), T3_2D, "drop", 60, 1.3, -5.0, "literal"),
+    ("D3Q19", (36, 20, 28), L.E8_3D, "bubble", 100, 1.0, -5.0, "literal"),
+    ("D3Q19", (24, 24, 24), L.E4_3D, "drop", 60, 0.8, -5.0, "literal"),
+]
+
+
+def _rho(kind, shape_xyz):
+    nx, ny = shape_xyz[0], shape_xyz[1]
+    nz = shape_xyz[2] if len(shape_xyz) > 2 else 1
+    if kind == "slab":
+        return L.tanh_slab(nx, ny, nz, 64, 192, 0.15, 1.9, 2.0)
+    R = min(nx, ny, nz if nz > 1 else nx) / 4.0
+    if kind == "drop":
+        return L.tanh_sphere(nx, ny, nz, R, 1.9, 0.15, 2.0)
+    return L.tanh_sphere(nx, ny, nz, R, 0.15, 1.9, 2.0)
+
+
+@pytest.mark.parametrize("lattice,shape,stencil,kind,steps,tau,G,conv", FP64_CASES)
+def test_fp64_bit_exact(lattice, shape, stencil, kind, steps, tau, G, conv):
+    rho = _rho(kind, shape)
+    lat, o = _run_pair(lattice, shape, stencil, rho, steps, "fp64", tau, G, conv)
+    f = lat.state()
+    assert np.array_equal(f, o.f), f"max diff {np.max(np.abs(f - o.f)):.3e}"
+    # fields of the state
+    rho_g, u_g = lat.fields()
+    fl = o.fields()
+    assert np.array_equal(rho_g, fl["n"])
+    assert np.array_equal(u_g, fl["u"])
+    # observables: compensated sums vs exact sums rounded once
+    ob = lat.observables()
+    ref = o.observables()
+    assert ob["status"] == P.LB_OK and ob["step"] == steps and ob["error_step"] == -1
+    assert ob["exp_ambiguous"] == 0
+    assert ob["mass"] == ref["mass"]
+    for k in range(3):
+        assert abs(ob["mom"][k] - ref["mom"][k]) <= 1e-15 * ref["mass"]
+    assert ob["umax"] == ref["umax"]
+    assert ob["rho_min"] == ref["rho_min"] and ob["rho_max"] == ref["rho_max"]
+    lat.close()
+
+
+@pytest.mark.parametrize("lattice,shape,stencil,kind,steps", [
+    ("D2Q9", (61, 47), L.E8_2D, "drop", 40),
+    ("D2Q9", (40, 37), T3_2D, "drop", 30),
+    ("D3Q19", (36, 20, 28), L.E8_3D, "bubble", 30),
+    ("D3Q19", (20, 18, 22), L.stencil_e4e6_tuning_8(3, Fr(-2, 7), Fr(1, 12)), "drop", 20),
+])
+def test_pressure_tensor_bit_exact(lattice, shape, stencil, kind, steps):
+    rho = _rho(kind, shape)
+    lat, o = _run_pair(lattice, shape, stencil, rho, steps, "fp64", 1.0, -5.0, "literal")
+    Pg = lat.pressure_tensor()
+    Po = o.pressure_tensor()
+    assert np.array_equal(Pg, Po), f"max diff {np.max(np.abs(Pg - Po)):.3e}"
+    lat.close()
+
+
+@pytest.mark.parametrize("lattice,shape,stencil,kind,steps,tau", [
+    ("D2Q9", (256, 4), L.E4_2D, "slab", 100, 1.0),
+    ("D2Q9", (61, 47), L.E8_2D, "drop", 100, 0.8),
+    ("D3Q19", (36, 20, 28), L.E8_3D, "bubble", 100, 1.0),
+    ("D3Q19", (33, 35, 31), L.E8_3D, "drop", 100, 0.9),
+])
+def test_fp32_shifted_density_within_1e5(lattice, shape, stencil, kind, steps, tau):
+    rho = _rho(kind, shape)
+    lat, o = _run_pair(lattice, shape, stencil, rho, steps, "fp32", tau, -5.0, "literal")
+    rho_g, _ = lat.fields()
+    rho_o = o.fields()["n"]
+    err = np.max(np.abs(rho_g - rho_o) / rho_o)
+    assert err < 1e-5, err
+    ob = lat.observables()
+    assert abs(ob["mass"] - o.observables()["mass"]) < 1e-6 * ob["mass"]
+    lat.close()
+
+
+def test_exp_cr_matches_oracle():
+    from tests.test_oracle_exp import _inputs
+    xs = np.array(_inputs() + list(-1.0 / np.linspace(0.03, 8.0, 2000)))
+    y, amb = P.lb_exp_cr(xs)
+    want = oracle.exp_cr_array(xs)
+    bad = np.nonzero(y != want)[0]
+    assert amb == 0
+    assert len(bad) == 0, [(xs[i], y[i], want[i]) for i in bad[:5]]
+
+
+def test_unstable_density_is_reported():
+    nx, ny = 16, 12
+    rho = np.full((1, ny, nx), 1.0)
+    lat = P.Lattice("D2Q9", (nx, ny), rho, L.E4_2D.bases, L.E4_2D.weights, precision="fp64")
+    lat.step(2)
+    assert lat.sync() == P.LB_OK
+    f = lat.state()
+    f[:, 0, 5, 7] = -0.2          # n < 0 at one node
+    lat.set_state(f)
+    lat.step(3)
+    assert lat.sync() == P.LB_EUNSTABLE
+    ob = lat.observables()
+    assert ob["status"] == P.LB_EUNSTABLE and ob["error_step"] == 2
+    lat.close()
+
+
+def test_step_before_stencil_and_bad_stencil():
+    rho = np.ones((1, 8, 8))
+    lat = P.Lattice("D2Q9", (8, 8), rho, precision="fp64")
+    with pytest.raises(P.LbError) as ei:
+        lat.step(1)
+    assert ei.value.status == P.LB_ESTATE
+    with pytest.raises(P.LbError) as ei:
+        lat.set_stencil([[1, 0], [0, 1]], [0.1, 0.2])     # same group twice
+    assert ei.value.status == P.LB_EINVAL
+    lat.close()
+
+
+def test_unsupported_pressure_tensor_group():
+    rho = np.ones((1, 12, 12))
+    lat = P.Lattice("D2Q9", (12, 12), rho, [[1, 0], [3, 1]], [0.2, 0.01], precision="fp64")
+    with pytest.raises(P.LbError) as ei:
+        lat.pressure_tensor()
+    assert ei.value.status == P.LB_EUNSUPPORTED
+    lat.close()
