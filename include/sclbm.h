@@ -205,6 +205,22 @@ lb_status lb_exp_cr(const double *x, double *y, long long n,
 /* Number of kernels this context has launched (for launch accounting). */
 long long lb_kernel_launches(const lb_ctx *ctx);
 
+/* Options of lb_set_option. */
+enum {
+    LB_OPT_FUSED = 1,   /* 1 (default): D3Q19 shifted-FP32 steps use the fused
+                           single-pass kernel when the stencil's groups are
+                           among the E8 groups and each dimension is >= 8;
+                           0: always the two-kernel path */
+    LB_OPT_ZCHUNK = 2   /* z planes marched by one CTA of the fused kernel
+                           (default 32) */
+};
+
+/* Set an option of the context.  LB_EINVAL for an unknown option or value. */
+lb_status lb_set_option(lb_ctx *ctx, int option, long long value);
+
+/* 1 if lb_step currently runs the fused single-pass kernel, else 0. */
+int lb_fused_active(const lb_ctx *ctx);
+
 /* Kernel kinds of the step, for lb_timing_read. */
 enum { LB_KERNEL_PSI = 0, LB_KERNEL_COLLIDE = 1, LB_KERNEL_FUSED = 2, LB_KERNEL_OTHER = 3,
        LB_KERNEL_KINDS = 4 };

@@ -81,6 +81,8 @@ _SIGS = {
     "lb_exp_cr": ([_dp, _dp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "lb_kernel_launches": ([_vp], ctypes.c_longlong),
     "lb_timing": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lb_set_option": ([_vp, ctypes.c_int, ctypes.c_longlong], ctypes.c_int),
+    "lb_fused_active": ([_vp], ctypes.c_int),
     "lb_timing_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -247,6 +249,17 @@ def lb_exp_cr(x):
 
 def lb_kernel_launches(ctx):
     return int(_lib.lb_kernel_launches(_vp(ctx)))
+
+
+LB_OPT_FUSED, LB_OPT_ZCHUNK = 1, 2
+
+
+def lb_set_option(ctx, option, value):
+    _check(_lib.lb_set_option(_vp(ctx), int(option), int(value)), "lb_set_option")
+
+
+def lb_fused_active(ctx):
+    return bool(_lib.lb_fused_active(_vp(ctx)))
 
 
 LB_KERNEL_PSI, LB_KERNEL_COLLIDE, LB_KERNEL_FUSED, LB_KERNEL_OTHER = range(4)

@@ -358,6 +358,8 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     c->g = {p->nx, p->ny, p->nz, N};
     set_consts(c);
     c->cur = 0;
+    c->fused_enabled = true;
+    c->fused_zchunk = 32;
     auto fail = [&](lb_status s) {
         lb_destroy(c);
         return s;
@@ -445,6 +447,7 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
         c->group_w[g] = gw[g];
     }
     c->stencil_set = true;
+    c->fast3d_ok = fused3d_applicable(c, c->fused_W, &c->fused_ng);
     if (c->graph_valid) {
         cudaGraphExecDestroy(c->graph);
         c->graph_valid = false;
@@ -575,5 +578,23 @@ lb_status lb_exp_cr(const double *x, double *y, long long n, long long *n_ambigu
 }
 
 long long lb_kernel_launches(const lb_ctx *c) { return c ? c->launches : 0; }
+
+lb_status lb_set_option(lb_ctx *c, int option, long long value) {
+    if (!c) return LB_EINVAL;
+    switch (option) {
+        case LB_OPT_FUSED:
+            c->fused_enabled = value != 0;
+            return LB_OK;
+        case LB_OPT_ZCHUNK:
+            if (value < 1 || value > 1 << 20) return LB_EINVAL;
+            c->fused_zchunk = (int)value;
+            return LB_OK;
+    }
+    return LB_EINVAL;
+}
+
+int lb_fused_active(const lb_ctx *c) {
+    return c && c->stencil_set && c->fast3d_ok && c->fused_enabled ? 1 : 0;
+}
 
 }  // extern "C"

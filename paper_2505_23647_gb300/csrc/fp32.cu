@@ -19,6 +19,8 @@ cudaError_t f32_init(lb_ctx *c, const double *rho, const double *u) {
 }
 
 cudaError_t f32_step(lb_ctx *c) {
+    if (c->Q == 19 && c->fast3d_ok && c->fused_enabled)
+        return f32_fused3d_step(c, c->fused_W, c->fused_ng);
     auto k = consts_as<float>(c->k);
     const float *A = (const float *)c->f[c->cur];
     float *B = (float *)c->f[1 - c->cur];
@@ -63,9 +65,8 @@ cudaError_t f32_fields(lb_ctx *c, double *n, double *u, double *mom) {
     auto k = consts_as<double>(c->k);
     int gb = grid_for(c->g.N);
     const float *A = (const float *)c->f[c->cur];
-    // widened populations keep their shift; k_fields64 needs unshifted f, so
-    // the FP32 path adds w_i rho0 through a shifted-consts trick: n already
-    // includes rho0, and j, u, j + F/2 do not depend on the shift.
+    // the widened populations keep their shift: n already includes rho0, and
+    // j, u and j + F/2 do not depend on it (sum_i w_i xi_i = 0)
     if (c->Q == 9)
         k_fields64<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, c->pairs64, k, n, n + c->g.N, u, mom);
     else

@@ -46,7 +46,7 @@ struct Flags {
     unsigned long long err_step;   // first failing step (ULLONG_MAX: none)
     unsigned long long step;       // steps completed on the device
     unsigned long long exp_amb;    // uncertified exp roundings
-    unsigned long long pad;
+    unsigned long long blocks_done;  // blocks finished in the current fused step
 };
 
 }  // namespace sclbm
@@ -64,6 +64,10 @@ struct lb_ctx {
     double group_w[LB_MAX_PAIRS];
     bool stencil_set;
     bool fast3d_ok;           // the fused FP32 D3Q19 path applies
+    bool fused_enabled;       // option LB_OPT_FUSED (default on)
+    float fused_W[7];         // group weights for the fused kernel
+    int fused_ng;             // number of E8 groups the fused kernel visits
+    int fused_zchunk;         // z planes per CTA (option LB_OPT_ZCHUNK)
     void *f[2];               // population buffers [Q][N] (post-collision, pre-stream)
     int cur;                  // buffer holding the current state
     void *psi;                // [N] psi of the precision in use
@@ -105,6 +109,9 @@ cudaError_t f32_fields(lb_ctx *c, double *n, double *u, double *mom);
 cudaError_t f32_get_state(lb_ctx *c, double *f);
 cudaError_t f32_set_state(lb_ctx *c, const double *f);
 cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi);
+// fused single-pass D3Q19 step (fused3d.cu)
+bool fused3d_applicable(const lb_ctx *c, float *W, int *ng);
+cudaError_t f32_fused3d_step(lb_ctx *c, const float *W, int ng);
 // precision-independent (fp64.cu): reductions, pressure tensor, exp diagnostic
 cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
                        double *out_host9);

@@ -16,8 +16,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def P():
-    from paper_2505_23647_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__._build_module().build()
     import paper_2505_23647_gb300 as pkg
     return pkg
 

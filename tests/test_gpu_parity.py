@@ -46,7 +46,10 @@ FP64_CASES = [
     ("D2Q9", (256, 4), L.E4_2D, "slab", 100, 1.0, -5.0, "literal"),
     ("D2Q9", (61, 47), L.E8_2D, "drop", 100, 0.8, -15.0, "paper"),
     ("D2Q9", (40, 37), T3_2D, "drop", 60, 1.3, -5.0, "literal"),
-    ("D3Q19", (36, 20, 28), L.E8_3D, "bubble", 100, 1.0, -5.0, "literal"),
+    # a bubble at G = -5 blows up within ~50 steps (the spinodal liquid
+    # filling a small box decomposes violently, in the oracle too); G = -4
+    # keeps it stable
+    ("D3Q19", (36, 20, 28), L.E8_3D, "bubble", 100, 1.0, -4.0, "literal"),
     ("D3Q19", (24, 24, 24), L.E4_3D, "drop", 60, 0.8, -5.0, "literal"),
 ]
 
@@ -94,7 +97,7 @@ def test_fp64_bit_exact(lattice, shape, stencil, kind, steps, tau, G, conv):
 ])
 def test_pressure_tensor_bit_exact(lattice, shape, stencil, kind, steps):
     rho = _rho(kind, shape)
-    lat, o = _run_pair(lattice, shape, stencil, rho, steps, "fp64", 1.0, -5.0, "literal")
+    lat, o = _run_pair(lattice, shape, stencil, rho, steps, "fp64", 1.0, -4.0, "literal")
     Pg = lat.pressure_tensor()
     Po = o.pressure_tensor()
     assert np.array_equal(Pg, Po), f"max diff {np.max(np.abs(Pg - Po)):.3e}"
@@ -104,7 +107,6 @@ def test_pressure_tensor_bit_exact(lattice, shape, stencil, kind, steps):
 @pytest.mark.parametrize("lattice,shape,stencil,kind,steps,tau", [
     ("D2Q9", (256, 4), L.E4_2D, "slab", 100, 1.0),
     ("D2Q9", (61, 47), L.E8_2D, "drop", 100, 0.8),
-    ("D3Q19", (36, 20, 28), L.E8_3D, "bubble", 100, 1.0),
     ("D3Q19", (33, 35, 31), L.E8_3D, "drop", 100, 0.9),
 ])
 def test_fp32_shifted_density_within_1e5(lattice, shape, stencil, kind, steps, tau):
@@ -164,3 +166,54 @@ def test_unsupported_pressure_tensor_group():
         lat.pressure_tensor()
     assert ei.value.status == P.LB_EUNSUPPORTED
     lat.close()
+
+
+def test_deep_quench_blow_up_reported_at_the_oracle_step():
+    """G = -5 bubble in a 36x20x28 box: the oracle's first n <= 0 step and the
+    GPU's reported error_step agree (bit-identical trajectories up to it)."""
+    shape = (36, 20, 28)
+    rho = _rho("bubble", shape)
+    o = oracle.Oracle("D3Q19", (28, 20, 36), L.E8_3D.groups, tau=1.0, G=-5.0)
+    o.init_equilibrium(rho)
+    rc = o.step(80)
+    assert rc > 0
+    lat = P.Lattice("D3Q19", shape, rho, L.E8_3D.bases, L.E8_3D.weights, precision="fp64",
+                    tau=1.0, G=-5.0)
+    lat.step(80)
+    assert lat.sync() == P.LB_EUNSTABLE
+    assert lat.observables()["error_step"] == rc - 1
+    lat.close()
+
+
+FUSED_CASES = [
+    # ragged in x (40 = 32 + 8), y (27 = 3*8 + 3) and z chunks (19 < 32)
+    ((40, 27, 19), L.E8_3D, 1.0, -4.0, 32),
+    ((40, 27, 19), L.E4_3D, 0.8, -5.0, 32),
+    # a stencil with a subset of the E8 groups (Table tab:e4_tuning_6, 3D)
+    ((33, 16, 24), L.stencil_e4_tuning_6(3, Fr(-1, 5)), 1.0, -4.0, 7),
+    ((64, 64, 64), L.E8_3D, 1.0, -4.0, 16),
+]
+
+
+@pytest.mark.parametrize("shape,stencil,tau,G,zchunk", FUSED_CASES)
+def test_fused_kernel_matches_oracle_and_two_kernel_path(shape, stencil, tau, G, zchunk):
+    rho = _rho("drop", shape)
+    steps = 20
+    res = {}
+    for fused in (1, 0):
+        lat = P.Lattice("D3Q19", shape, rho, stencil.bases, stencil.weights, precision="fp32",
+                        tau=tau, G=G)
+        P.lb_set_option(lat.ctx, P.LB_OPT_FUSED, fused)
+        P.lb_set_option(lat.ctx, P.LB_OPT_ZCHUNK, zchunk)
+        assert P.lb_fused_active(lat.ctx) == bool(fused)
+        lat.step(steps)
+        assert lat.sync() == P.LB_OK
+        res[fused] = lat.fields()[0]
+        lat.close()
+    o = oracle.Oracle("D3Q19", shape[::-1], stencil.groups, tau=tau, G=G)
+    o.init_equilibrium(rho)
+    o.step(steps)
+    n = o.fields()["n"]
+    for fused in (1, 0):
+        err = np.max(np.abs(res[fused] - n) / n)
+        assert err < 1e-5, (fused, err)
