@@ -377,9 +377,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-literal", action="store_true")
+    ap.add_argument("--size", type=int, default=256,
+                    help="cube edge (default 256, the workload; smaller only for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global NX, NY, NZ, RADIUS
+    if args.size != 256:
+        NX = NY = NZ = args.size
+        RADIUS = 40.0 * args.size / 256.0
     dist, rank, ws = _dist()
     try:
         if args.impl == "reference":

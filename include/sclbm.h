@@ -86,7 +86,7 @@ typedef struct lb_params {
     int g_convention;   /* LB_G_LITERAL or LB_G_TIMES_CS2 */
     int psi_kind;       /* LB_PSI_EXP: psi = exp(-1/n) */
     double psi_eps;     /* reserved, 0 */
-    double rho0_shift;  /* rho0 of the FP32 shift g_i = f_i - w_i rho0 */
+    double rho0_shift;  /* rho0 of the FP32 shift g_i = f_i - w_i rho0 (default 0.5) */
 } lb_params;
 
 typedef struct lb_stencil_info {
@@ -118,7 +118,9 @@ const char *lb_status_str(lb_status s);
 const char *lb_last_cuda_error(void);
 
 /* Fill *p with defaults: D2Q9 64x64x1, FP64, tau 1, G -5, literal G,
- * psi = exp(-1/n), rho0_shift 1. */
+ * psi = exp(-1/n), rho0_shift 0.5 (the shift keeps binary32 rounding of
+ * both gas, n ~ 0.1-0.6, and liquid, n ~ 1.7-5.5, populations small; it
+ * measured 2-5x more accurate than 1.0 on Shan-Chen droplets). */
 lb_status lb_params_default(lb_params *p);
 
 /* Expand symmetry groups into the canonical (e,-e) pair list (host only, no

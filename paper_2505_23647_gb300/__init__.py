@@ -130,7 +130,7 @@ def lb_params_default():
 
 
 def make_params(lattice="D2Q9", shape=(64, 64), precision="fp64", tau=1.0, G=-5.0,
-                convention="literal", rho0_shift=1.0):
+                convention="literal", rho0_shift=0.5):
     """lb_params from Python values; shape is (nx, ny) or (nx, ny, nz)."""
     p = lb_params_default()
     p.lattice = {"D2Q9": LB_D2Q9, "D3Q19": LB_D3Q19}[lattice]
@@ -283,7 +283,7 @@ class Lattice:
     Arrays in and out are numpy with shape (nz, ny, nx) / (C, nz, ny, nx)."""
 
     def __init__(self, lattice, shape_xyz, rho, stencil_bases=None, stencil_weights=None,
-                 precision="fp64", tau=1.0, G=-5.0, convention="literal", rho0_shift=1.0,
+                 precision="fp64", tau=1.0, G=-5.0, convention="literal", rho0_shift=0.5,
                  u=None, stream=None):
         self.params = make_params(lattice, shape_xyz, precision, tau, G, convention, rho0_shift)
         self.D = 2 if lattice == "D2Q9" else 3

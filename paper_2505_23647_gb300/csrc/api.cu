@@ -313,7 +313,7 @@ lb_status lb_params_default(lb_params *p) {
     p->g_convention = LB_G_LITERAL;
     p->psi_kind = LB_PSI_EXP;
     p->psi_eps = 0.0;
-    p->rho0_shift = 1.0;
+    p->rho0_shift = 0.5;
     return LB_OK;
 }
 

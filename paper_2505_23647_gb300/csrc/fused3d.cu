@@ -89,12 +89,51 @@ __device__ __forceinline__ float dens(const float *g) {
     return ((a + b) + (c + d)) + e;
 }
 
+// asynchronous 4-byte global -> shared copy (cp.async, L1-allocating)
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// stage the pulled populations of one plane (tile plus halo) into shared
+// memory: stage[i * EXY + node] = A_i(node - xi_i)
+template <int EXY>
+__device__ __forceinline__ void stage_plane(const float *__restrict__ A, float *stage, int node,
+                                            const int *ro, const int *zo, int N) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = cvel<19>(i, 0), cy = cvel<19>(i, 1), cz = cvel<19>(i, 2);
+        cp_async4(stage + i * EXY + node, A + (i * N + zo[cz + 1] + ro[(cy + 1) * 3 + (cx + 1)]));
+    }
+}
+
+template <int EXY>
+__device__ __forceinline__ float psi_from_stage(const float *stage, int node, float rho0, bool &bad) {
+    float g[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) g[i] = stage[i * EXY + node];
+    const float n = dens(g) + rho0;
+    bad |= !(n > 0.f);
+    return expf(-__frcp_rn(n));
+}
+
+__device__ __forceinline__ void plane_offsets(int zz, const Params &p, int *zo) {
+    zo[0] = wrap1(zz + 1, p.nz) * p.plane;   // c_z = -1: source at zz + 1
+    zo[1] = zz * p.plane;
+    zo[2] = wrap1(zz - 1, p.nz) * p.plane;   // c_z = +1: source at zz - 1
+}
+
 template <int R, int NG>
 __global__ void __launch_bounds__(TX * TY, 2)
     k_fused3d(const float *__restrict__ A, float *__restrict__ B, const Params p, Flags *flags) {
-    constexpr int EX = TX + 2 * R, EY = TY + 2 * R, NS = 2 * R + 2;
-    constexpr int HALO = EX * EY - TX * TY;
-    __shared__ float ring[NS * EY * EX];
+    constexpr int EX = TX + 2 * R, EY = TY + 2 * R, NS = 2 * R + 2, EXY = EX * EY;
+    constexpr int HALO = EXY - TX * TY;
+    extern __shared__ float smem[];
+    float *ring = smem;                          // NS planes of psi
+    float *stage0 = smem + NS * EXY;             // two planes of staged populations
+    float *stage1 = stage0 + 19 * EXY;
 
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -134,61 +173,59 @@ __global__ void __launch_bounds__(TX * TY, 2)
     bool bad = false;
 
     const int nit = (z1 - z0) + 2 * R;
+    {   // stage the first plane
+        int zo[3];
+        plane_offsets(wrap1(z0 - R, p.nz), p, zo);
+        stage_plane<EXY>(A, stage0, cen, ro_i, zo, p.N);
+        if (has_halo) stage_plane<EXY>(A, stage0, hof, ro_h, zo, p.N);
+        cp_commit();
+    }
     for (int it = 0; it < nit; ++it) {
         const int zz = wrap1(z0 - R + it, p.nz);
-        int zo[3];
-        zo[0] = wrap1(zz + 1, p.nz) * p.plane;   // c_z = -1: source at zz + 1
-        zo[1] = zz * p.plane;
-        zo[2] = wrap1(zz - 1, p.nz) * p.plane;   // c_z = +1: source at zz - 1
-        float *slot = ring + (it % NS) * (EY * EX);
-        {
-            float g[19];
-            pull19(A, ro_i, zo, p.N, g);
-            const float n = dens(g) + p.rho0;
-            bad |= !(n > 0.f);
-            slot[cen] = expf(-__frcp_rn(n));
+        float *cur = (it & 1) ? stage1 : stage0;
+        float *nxt = (it & 1) ? stage0 : stage1;
+        // prefetch plane it + 1 while this one is consumed
+        if (it + 1 < nit) {
+            int zo[3];
+            plane_offsets(wrap1(zz + 1, p.nz), p, zo);
+            stage_plane<EXY>(A, nxt, cen, ro_i, zo, p.N);
+            if (has_halo) stage_plane<EXY>(A, nxt, hof, ro_h, zo, p.N);
         }
+        cp_commit();
+        cp_wait1();
+        __syncthreads();
+        float *slot = ring + (it % NS) * EXY;
+        slot[cen] = psi_from_stage<EXY>(cur, cen, p.rho0, bad);
         if (has_halo) {
-            float g[19];
-            pull19(A, ro_h, zo, p.N, g);
-            const float n = dens(g) + p.rho0;
-            slot[hof] = expf(-__frcp_rn(n));
+            bool dummy = false;
+            slot[hof] = psi_from_stage<EXY>(cur, hof, p.rho0, dummy);
         }
         __syncthreads();
         if (it < 2 * R) continue;
         // ---- collide plane zc = zz - R --------------------------------------
         const int zc = wrap1(zz - R, p.nz);
+        int zoc[3];
+        plane_offsets(zc, p, zoc);
+        float g[19];
+        pull19(A, ro_i, zoc, p.N, g);            // in flight during the force loop
         const float *pz[2 * R + 1];
 #pragma unroll
-        for (int k = -R; k <= R; ++k) pz[k + R] = ring + ((it - R + k + NS) % NS) * (EY * EX) + cen;
-        float acc[NG][3];
-#pragma unroll
-        for (int gq = 0; gq < NG; ++gq) acc[gq][0] = acc[gq][1] = acc[gq][2] = 0.f;
+        for (int k = -R; k <= R; ++k) pz[k + R] = ring + ((it - R + k + NS) % NS) * EXY + cen;
+        float F[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < group_end(NG - 1); ++a) {
             const int ex = pair_c(a, 0), ey = pair_c(a, 1), ez = pair_c(a, 2), gq = pair_c(a, 3);
             const float d = pz[R + ez][ey * EX + ex] - pz[R - ez][-ey * EX - ex];
-            if (ex) acc[gq][0] = fmaf((float)ex, d, acc[gq][0]);
-            if (ey) acc[gq][1] = fmaf((float)ey, d, acc[gq][1]);
-            if (ez) acc[gq][2] = fmaf((float)ez, d, acc[gq][2]);
+            if (ex) F[0] = fmaf(ex == 1 ? p.W[gq] : ex == -1 ? -p.W[gq] : (float)ex * p.W[gq], d, F[0]);
+            if (ey) F[1] = fmaf(ey == 1 ? p.W[gq] : ey == -1 ? -p.W[gq] : (float)ey * p.W[gq], d, F[1]);
+            if (ez) F[2] = fmaf(ez == 1 ? p.W[gq] : ez == -1 ? -p.W[gq] : (float)ez * p.W[gq], d, F[2]);
         }
-        float F[3];
         {
             const float pre = p.mGp * pz[R][0];
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) {
-                float s = 0.f;
-#pragma unroll
-                for (int gq = 0; gq < NG; ++gq) s = fmaf(p.W[gq], acc[gq][mu], s);
-                F[mu] = pre * s;
-            }
+            F[0] *= pre;
+            F[1] *= pre;
+            F[2] *= pre;
         }
-        int zoc[3];
-        zoc[0] = wrap1(zc + 1, p.nz) * p.plane;
-        zoc[1] = zc * p.plane;
-        zoc[2] = wrap1(zc - 1, p.nz) * p.plane;
-        float g[19];
-        pull19(A, ro_i, zoc, p.N, g);
         const float dn = dens(g);
         const float n = dn + p.rho0;
         const float inv = __frcp_rn(n);
@@ -249,6 +286,11 @@ __global__ void __launch_bounds__(TX * TY, 2)
     }
 }
 
+template <int R>
+constexpr int smem_bytes() {
+    return (2 * R + 2 + 2 * 19) * (TX + 2 * R) * (TY + 2 * R) * 4;
+}
+
 }  // namespace fz
 
 bool fused3d_applicable(const lb_ctx *c, float *W, int *ng) {
@@ -295,18 +337,30 @@ cudaError_t f32_fused3d_step(lb_ctx *c, const float *W, int ng) {
     const float *A = (const float *)c->f[c->cur];
     float *B = (float *)c->f[1 - c->cur];
     tm_begin(c, LB_KERNEL_FUSED);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(fz::k_fused3d<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<1>());
+        cudaFuncSetAttribute(fz::k_fused3d<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<1>());
+        cudaFuncSetAttribute(fz::k_fused3d<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<1>());
+        cudaFuncSetAttribute(fz::k_fused3d<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
+        cudaFuncSetAttribute(fz::k_fused3d<2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
+        cudaFuncSetAttribute(fz::k_fused3d<2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
+        cudaFuncSetAttribute(fz::k_fused3d<2, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
+        attr_done = true;
+    }
+    const int sm1 = fz::smem_bytes<1>(), sm2 = fz::smem_bytes<2>();
     if (ng <= 3) {
         switch (ng) {
-            case 1: fz::k_fused3d<1, 1><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
-            case 2: fz::k_fused3d<1, 2><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
-            default: fz::k_fused3d<1, 3><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
+            case 1: fz::k_fused3d<1, 1><<<grid, block, sm1, c->stream>>>(A, B, p, c->flags); break;
+            case 2: fz::k_fused3d<1, 2><<<grid, block, sm1, c->stream>>>(A, B, p, c->flags); break;
+            default: fz::k_fused3d<1, 3><<<grid, block, sm1, c->stream>>>(A, B, p, c->flags); break;
         }
     } else {
         switch (ng) {
-            case 4: fz::k_fused3d<2, 4><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
-            case 5: fz::k_fused3d<2, 5><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
-            case 6: fz::k_fused3d<2, 6><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
-            default: fz::k_fused3d<2, 7><<<grid, block, 0, c->stream>>>(A, B, p, c->flags); break;
+            case 4: fz::k_fused3d<2, 4><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
+            case 5: fz::k_fused3d<2, 5><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
+            case 6: fz::k_fused3d<2, 6><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
+            default: fz::k_fused3d<2, 7><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
         }
     }
     tm_end(c);
