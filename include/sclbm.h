@@ -213,14 +213,18 @@ enum {
                            single-pass kernel when the stencil's groups are
                            among the E8 groups and each dimension is >= 8;
                            0: always the two-kernel path */
-    LB_OPT_ZCHUNK = 2   /* z planes marched by one CTA of the fused kernel
+    LB_OPT_ZCHUNK = 2,  /* z planes marched by one CTA of the fused kernel
                            (default 32) */
+    LB_OPT_TMA = 3      /* 1 (default): on lattices with nx % 32 == 0,
+                           ny % 8 == 0, nz >= 8 the fused kernel stages planes
+                           with TMA; 0: with per-thread cp.async */
 };
 
 /* Set an option of the context.  LB_EINVAL for an unknown option or value. */
 lb_status lb_set_option(lb_ctx *ctx, int option, long long value);
 
-/* 1 if lb_step currently runs the fused single-pass kernel, else 0. */
+/* 0 if lb_step runs the two-kernel path, 1 the fused single-pass kernel
+ * with cp.async staging, 2 the fused kernel with TMA staging. */
 int lb_fused_active(const lb_ctx *ctx);
 
 /* Kernel kinds of the step, for lb_timing_read. */

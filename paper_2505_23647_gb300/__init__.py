@@ -251,7 +251,7 @@ def lb_kernel_launches(ctx):
     return int(_lib.lb_kernel_launches(_vp(ctx)))
 
 
-LB_OPT_FUSED, LB_OPT_ZCHUNK = 1, 2
+LB_OPT_FUSED, LB_OPT_ZCHUNK, LB_OPT_TMA = 1, 2, 3
 
 
 def lb_set_option(ctx, option, value):
@@ -259,7 +259,8 @@ def lb_set_option(ctx, option, value):
 
 
 def lb_fused_active(ctx):
-    return bool(_lib.lb_fused_active(_vp(ctx)))
+    """0: two-kernel path, 1: fused kernel (cp.async), 2: fused kernel (TMA)."""
+    return int(_lib.lb_fused_active(_vp(ctx)))
 
 
 LB_KERNEL_PSI, LB_KERNEL_COLLIDE, LB_KERNEL_FUSED, LB_KERNEL_OTHER = range(4)

@@ -25,6 +25,7 @@ UNITS = {
     "fp64.cu": ["-fmad=false"],
     "fp32.cu": [],
     "fused3d.cu": [],
+    "fused3d_tma.cu": [],
 }
 
 

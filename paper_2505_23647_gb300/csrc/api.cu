@@ -215,6 +215,11 @@ lb_status ensure_scratch(lb_ctx *c, size_t bytes) {
 lb_status check_flags(lb_ctx *c, Flags *h) {
     CK(cudaMemcpyAsync(h, c->flags, sizeof(Flags), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (h->timeouts) {
+        std::snprintf(g_cuda_err, sizeof g_cuda_err,
+                      "fused kernel: %llu bounded barrier waits gave up", h->timeouts);
+        return LB_ECUDA;
+    }
     return h->err_step != ULLONG_MAX ? LB_EUNSTABLE : LB_OK;
 }
 
@@ -355,10 +360,17 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     c->p = *p;
     c->D = p->lattice == LB_D2Q9 ? 2 : 3;
     c->Q = p->lattice == LB_D2Q9 ? 9 : 19;
-    c->g = {p->nx, p->ny, p->nz, N};
+    // shifted-FP32 D3Q19 lattices that tile exactly get periodic ghost
+    // columns (4 each side) and rows (3 each side) for the TMA kernel
+    c->padded = p->precision == LB_FP32_SHIFTED && p->lattice == LB_D3Q19 && p->nx % 32 == 0 &&
+                p->ny % 8 == 0 && p->nz >= 8;
+    const int ox = c->padded ? 4 : 0, oy = c->padded ? 3 : 0;
+    c->g = {p->nx, p->ny, p->nz, N, p->nx + 2 * ox, p->ny + 2 * oy, ox, oy,
+            (long long)(p->nx + 2 * ox) * (p->ny + 2 * oy) * p->nz};
     set_consts(c);
     c->cur = 0;
     c->fused_enabled = true;
+    c->fused_tma = true;
     c->fused_zchunk = 32;
     auto fail = [&](lb_status s) {
         lb_destroy(c);
@@ -373,7 +385,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
         c->own_stream = true;
     }
-    const size_t fbytes = (size_t)c->Q * N * tsize(c);
+    const size_t fbytes = (size_t)c->Q * c->g.Np * tsize(c);
     for (int b = 0; b < 2; ++b) {
         e = cudaMalloc(&c->f[b], fbytes);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(f)"));
@@ -384,7 +396,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(flags)"));
     e = cudaMalloc(&c->red, 1024 * 128);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(red)"));
-    Flags h0 = {ULLONG_MAX, 0, 0, 0};
+    Flags h0 = {ULLONG_MAX, 0, 0, 0, 0};
     e = cudaMemcpyAsync(c->flags, &h0, sizeof h0, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(flags)"));
     lb_status s = ensure_scratch(c, (size_t)(1 + c->D) * N * sizeof(double));
@@ -395,6 +407,12 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     if (u_init) {
         e = cudaMemcpyAsync(u_d, u_init, c->D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(u)"));
+    }
+    if (c->padded) {
+        e = cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset(f)"));
+        c->tma_ok = tma_make_maps(c);
     }
     e = p->precision == LB_FP64 ? f64_init(c, rho_d, u_d) : f32_init(c, rho_d, u_d);
     if (e != cudaSuccess) return fail(cuda_fail(e, "init kernel"));
@@ -585,6 +603,9 @@ lb_status lb_set_option(lb_ctx *c, int option, long long value) {
         case LB_OPT_FUSED:
             c->fused_enabled = value != 0;
             return LB_OK;
+        case LB_OPT_TMA:
+            c->fused_tma = value != 0;
+            return LB_OK;
         case LB_OPT_ZCHUNK:
             if (value < 1 || value > 1 << 20) return LB_EINVAL;
             c->fused_zchunk = (int)value;
@@ -594,7 +615,8 @@ lb_status lb_set_option(lb_ctx *c, int option, long long value) {
 }
 
 int lb_fused_active(const lb_ctx *c) {
-    return c && c->stencil_set && c->fast3d_ok && c->fused_enabled ? 1 : 0;
+    if (!(c && c->stencil_set && c->fast3d_ok && c->fused_enabled)) return 0;
+    return c->tma_ok && c->fused_tma ? 2 : 1;
 }
 
 }  // extern "C"

@@ -6,6 +6,14 @@
 
 namespace sclbm {
 
+cudaError_t ghosts_refresh(lb_ctx *c) {
+    if (!c->padded) return cudaSuccess;
+    const long long total = (long long)c->g.nxp * c->g.nyp * c->g.nz * c->Q;
+    k_ghosts<float><<<grid_for(total), 256, 0, c->stream>>>((float *)c->f[c->cur], c->g, c->Q);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t f32_init(lb_ctx *c, const double *rho, const double *u) {
     auto k = consts_as<double>(c->k);
     int gb = grid_for(c->g.N);
@@ -15,7 +23,8 @@ cudaError_t f32_init(lb_ctx *c, const double *rho, const double *u) {
     else
         k_init<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, rho, u, k);
     c->launches++;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : ghosts_refresh(c);
 }
 
 cudaError_t f32_step(lb_ctx *c) {
@@ -45,7 +54,8 @@ cudaError_t f32_step(lb_ctx *c) {
     }
     c->launches += 2;
     c->cur = 1 - c->cur;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : ghosts_refresh(c);
 }
 
 cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi) {
@@ -96,7 +106,8 @@ cudaError_t f32_set_state(lb_ctx *c, const double *f) {
     else
         k_set_state<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
     c->launches++;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    return e != cudaSuccess ? e : ghosts_refresh(c);
 }
 
 }  // namespace sclbm

@@ -1,6 +1,7 @@
 // internal.h -- context layout and kernel launchers shared by the library's
 // translation units (not part of the public ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,7 +39,10 @@ struct Consts {
 
 struct Geom {
     int nx, ny, nz;
-    long long N;
+    long long N;        // nodes
+    int nxp, nyp;       // padded plane of the population arrays
+    int ox, oy;         // offset of node (0,0) inside a padded plane
+    long long Np;       // population stride (nxp * nyp * nz)
 };
 
 // Device-side counters of a context.
@@ -47,6 +51,7 @@ struct Flags {
     unsigned long long step;       // steps completed on the device
     unsigned long long exp_amb;    // uncertified exp roundings
     unsigned long long blocks_done;  // blocks finished in the current fused step
+    unsigned long long timeouts;     // bounded barrier waits that gave up
 };
 
 }  // namespace sclbm
@@ -68,6 +73,10 @@ struct lb_ctx {
     float fused_W[7];         // group weights for the fused kernel
     int fused_ng;             // number of E8 groups the fused kernel visits
     int fused_zchunk;         // z planes per CTA (option LB_OPT_ZCHUNK)
+    bool padded;              // populations carry periodic ghost columns/rows
+    bool tma_ok;              // tensor maps built for the padded buffers
+    bool fused_tma;           // option LB_OPT_TMA (default on)
+    CUtensorMap tmap[2][2];   // [buffer][R-1] psi-plane boxes for the TMA kernel
     void *f[2];               // population buffers [Q][N] (post-collision, pre-stream)
     int cur;                  // buffer holding the current state
     void *psi;                // [N] psi of the precision in use
@@ -112,6 +121,9 @@ cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi);
 // fused single-pass D3Q19 step (fused3d.cu)
 bool fused3d_applicable(const lb_ctx *c, float *W, int *ng);
 cudaError_t f32_fused3d_step(lb_ctx *c, const float *W, int ng);
+cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng);
+bool tma_make_maps(lb_ctx *c);
+cudaError_t ghosts_refresh(lb_ctx *c);   // padded layouts: refresh ghost cells of f[cur]
 // precision-independent (fp64.cu): reductions, pressure tensor, exp diagnostic
 cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
                        double *out_host9);

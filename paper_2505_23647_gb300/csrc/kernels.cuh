@@ -42,8 +42,16 @@ __device__ __forceinline__ int wrapi(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
+// node index (x fastest) of fields with one value per node
 __device__ __forceinline__ long long site(const Geom &g, int x, int y, int z) {
     return ((long long)wrapi(z, g.nz) * g.ny + wrapi(y, g.ny)) * g.nx + wrapi(x, g.nx);
+}
+
+// index of a node inside one population plane block; population arrays may
+// carry periodic ghost columns/rows (ox, oy) around every x-y plane
+__device__ __forceinline__ long long popidx(const Geom &g, int x, int y, int z) {
+    return ((long long)wrapi(z, g.nz) * g.nyp + (wrapi(y, g.ny) + g.oy)) * g.nxp +
+           (wrapi(x, g.nx) + g.ox);
 }
 
 __device__ __forceinline__ void coords(const Geom &g, long long s, int &x, int &y, int &z) {
@@ -95,8 +103,8 @@ __device__ __forceinline__ void pull(const T *__restrict__ A, const Geom &g, int
                                      int z, T *fi) {
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-        fi[i] = A[(long long)i * g.N +
-                  site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+        fi[i] = A[(long long)i * g.Np +
+                  popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
 }
 
 template <typename T, int Q>
@@ -214,7 +222,9 @@ __global__ void __launch_bounds__(256) k_collide(const T *__restrict__ A, T *__r
         T fo[Q];
         collide<T, D, Q, SHIFT>(fi, n, dn, F, k, fo, nullptr, nullptr);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) B[(long long)i * g.N + s] = fo[i];
+        const long long ps = popidx(g, x, y, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) B[(long long)i * g.Np + ps] = fo[i];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) flags->step = flags->step + 1;
 }
@@ -231,8 +241,8 @@ __global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,
         double fi[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            fi[i] = (double)A[(long long)i * g.N +
-                              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+            fi[i] = (double)A[(long long)i * g.Np +
+                              popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
         double n = sum_q<double, Q>(fi);
         if (SHIFT) n = n + rho0;
         n_out[s] = n;
@@ -253,8 +263,8 @@ __global__ void k_fields64(const T *__restrict__ A, Geom g, const PairsF64 P, Co
         double fi[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            fi[i] = (double)A[(long long)i * g.N +
-                              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+            fi[i] = (double)A[(long long)i * g.Np +
+                              popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
         const double n = n_in[s];
         double acc[3];
         force_acc<double, PairsF64, D>(psi, g, x, y, z, P, acc);
@@ -294,8 +304,8 @@ __global__ void k_init(T *__restrict__ A, Geom g, const double *__restrict__ rho
             const double cu = cdot<Q, D, double>(i, us);
             double f = (k.w[i] * n) * (((1.0 + 3.0 * cu) + 4.5 * (cu * cu)) - 1.5 * uu);
             if (SHIFT) f = f - k.w[i] * k.rho0;
-            A[(long long)i * g.N +
-              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)f;
+            A[(long long)i * g.Np +
+              popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)f;
         }
     }
 }
@@ -309,8 +319,8 @@ __global__ void k_get_state(const T *__restrict__ A, Geom g, double *__restrict_
         coords(g, s, x, y, z);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            double v = (double)A[(long long)i * g.N +
-                                 site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
+            double v = (double)A[(long long)i * g.Np +
+                                 popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
             if (SHIFT) v = v + k.w[i] * k.rho0;
             out[(long long)i * g.N + s] = v;
         }
@@ -328,9 +338,28 @@ __global__ void k_set_state(T *__restrict__ A, Geom g, const double *__restrict_
         for (int i = 0; i < Q; ++i) {
             double v = in[(long long)i * g.N + s];
             if (SHIFT) v = v - k.w[i] * k.rho0;
-            A[(long long)i * g.N +
-              site(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)v;
+            A[(long long)i * g.Np +
+              popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)v;
         }
+    }
+}
+
+// Refresh the periodic ghost columns/rows of every population plane from
+// the nodes they mirror (padded layouts only).
+template <typename T>
+__global__ void k_ghosts(T *__restrict__ A, Geom g, int Q) {
+    const long long plane = (long long)g.nxp * g.nyp;
+    const long long total = plane * g.nz * Q;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
+        const long long r = k % plane;
+        const int yp = (int)(r / g.nxp), xp = (int)(r - (long long)yp * g.nxp);
+        const int xl = xp - g.ox, yl = yp - g.oy;
+        if (xl >= 0 && xl < g.nx && yl >= 0 && yl < g.ny) continue;
+        const long long zi = k / plane;   // i * nz + z
+        const long long src = zi * plane + (long long)(wrapi(yl, g.ny) + g.oy) * g.nxp +
+                              (wrapi(xl, g.nx) + g.ox);
+        A[k] = A[src];
     }
 }
 
