@@ -114,17 +114,42 @@ __device__ __forceinline__ float psi_from_boxes(const float *stage, int ex, int 
     return psi32(n);
 }
 
+// issue the 19 population boxes of the tile's collision plane zc (rows
+// y0 - c_y .. y0 + TY - c_y, the same 40 columns)
+__device__ __forceinline__ void issue_collision_plane(const CUtensorMap *map, float *stage,
+                                                      unsigned long long *bar, int zc, int x0,
+                                                      int y0, const Params &p) {
+    constexpr int BOX = TY * BOXW;
+    mbar_expect_tx(bar, 19u * BOX * 4u);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cy = cvel<19>(i, 1), cz = cvel<19>(i, 2);
+        tma_load_3d(stage + i * BOX, map, x0 + p.ox - 4, y0 + p.oy - cy,
+                    i * p.nz + wrap1(zc - cz, p.nz), bar);
+    }
+}
+
+// Schedule of one CTA (it = 0 .. nit-1, zz = z0 - R + it, zc = zz - R):
+//   wait psi-stage(it); psi(zz) -> ring; barrier (+ timeout vote);
+//   thread 0 issues psi-stage(it+1) into the single psi stage (all reads of
+//   it are behind the barrier) and collision-stage(it+1) into buffer
+//   (it+1)&1 (its last reader, collision(it-1), is behind the barrier too);
+//   force(zc) from the ring; wait collision-stage(it); collide; store.
+// Both copies therefore overlap at least the force and collision phase of
+// the iteration before they are needed.
 template <int R, int NG>
 __global__ void __launch_bounds__(TX * TY, 2)
-    k_fused3d_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ A,
+    k_fused3d_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap cmap,
                   float *__restrict__ B, const Params p, Flags *flags) {
     constexpr int EX = TX + 2 * R, EY = TY + 2 * R, NS = 2 * R + 2, EXY = EX * EY;
     constexpr int HALO = EXY - TX * TY;
     constexpr int STAGE = 19 * box_stride<R>();
+    constexpr int CSTAGE = 19 * TY * BOXW;
     extern __shared__ __align__(128) float smem[];
-    float *stage0 = smem;
-    float *stage1 = smem + STAGE;
-    float *ring = smem + 2 * STAGE;
+    float *stage = smem;                          // psi plane: 19 boxes, tile + halo
+    float *cst0 = smem + STAGE;                   // collision plane, two buffers
+    float *cst1 = cst0 + CSTAGE;
+    float *ring = cst1 + CSTAGE;                  // NS planes of psi
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(ring + NS * EXY);
 
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
@@ -137,59 +162,42 @@ __global__ void __launch_bounds__(TX * TY, 2)
     if (has_halo) halo_coords<R>(t, hx, hy);
     const int cen = (ty + R) * EX + (tx + R);
     const int hof = hy * EX + hx;
-    // the node's pull sources inside a padded plane
-    int ro[9];
-#pragma unroll
-    for (int cy = -1; cy <= 1; ++cy)
-#pragma unroll
-        for (int cx = -1; cx <= 1; ++cx)
-            ro[(cy + 1) * 3 + (cx + 1)] = (yi - cy + p.oy) * p.nxp + (xi - cx + p.ox);
     bool bad = false;
 
     if (t == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(&bar[0], 1);   // psi stage full
+        mbar_init(&bar[1], 1);   // collision buffer 0 full
+        mbar_init(&bar[2], 1);   // collision buffer 1 full
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
     const int nit = (z1 - z0) + 2 * R;
-    if (t == 0) issue_plane<R>(&map, stage0, &bar[0], wrap1(z0 - R, p.nz), x0, y0, p);
+    if (t == 0) issue_plane<R>(&map, stage, &bar[0], wrap1(z0 - R, p.nz), x0, y0, p);
     bool timed_out = false, late = false;
     for (int it = 0; it < nit; ++it) {
         const int zz = wrap1(z0 - R + it, p.nz);
-        const int b = it & 1;
-        float *cur = b ? stage1 : stage0;
-        if (t == 0 && it + 1 < nit) {
-            // the other stage was last read before the previous iteration's
-            // barrier; order those reads before the async-proxy writes
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            issue_plane<R>(&map, b ? stage0 : stage1, &bar[1 - b], wrap1(zz + 1, p.nz), x0, y0, p);
-        }
-        // pull the collision plane's populations now: the loads fly while psi
-        // is formed, published and the force is summed
-        float g[19];
-        if (it >= 2 * R) {
-            const int zc = wrap1(zz - R, p.nz);
-            const int zo[3] = {wrap1(zc + 1, p.nz) * p.pplane, zc * p.pplane,
-                               wrap1(zc - 1, p.nz) * p.pplane};
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                const int cx = cvel<19>(i, 0), cy = cvel<19>(i, 1), cz = cvel<19>(i, 2);
-                g[i] = __ldg(A + i * p.Np + zo[cz + 1] + ro[(cy + 1) * 3 + (cx + 1)]);
-            }
-        }
         // each thread's own wait makes the stage visible to it; the vote on
         // a timed-out wait rides on the barrier that publishes psi
-        const bool ok = mbar_wait_bounded(&bar[b], (unsigned)(it >> 1) & 1u);
+        const bool ok = mbar_wait_bounded(&bar[0], (unsigned)it & 1u);
         float *slot = ring + (it % NS) * EXY;
-        slot[cen] = psi_from_boxes<R>(cur, tx + R, ty + R, p.rho0, bad);
+        slot[cen] = psi_from_boxes<R>(stage, tx + R, ty + R, p.rho0, bad);
         if (has_halo) {
             bool dummy = false;
-            slot[hof] = psi_from_boxes<R>(cur, hx, hy, p.rho0, dummy);
+            slot[hof] = psi_from_boxes<R>(stage, hx, hy, p.rho0, dummy);
         }
         if (!__syncthreads_and(ok && !late)) {
             timed_out = true;
             break;
+        }
+        if (t == 0) {
+            // the stages' previous readers are all behind the barrier above;
+            // order their generic-proxy reads before the async-proxy writes
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            if (it + 1 < nit)
+                issue_plane<R>(&map, stage, &bar[0], wrap1(zz + 1, p.nz), x0, y0, p);
+            if (it + 1 >= 2 * R && it + 1 < nit)
+                issue_collision_plane(&cmap, ((it + 1) & 1) ? cst1 : cst0, &bar[1 + ((it + 1) & 1)],
+                                      wrap1(zz + 1 - R, p.nz), x0, y0, p);
         }
         if (it < 2 * R) continue;
         // ---- collide plane zc = zz - R --------------------------------------
@@ -199,6 +207,16 @@ __global__ void __launch_bounds__(TX * TY, 2)
         for (int k = -R; k <= R; ++k) pz[k + R] = ring + ((it - R + k + NS) % NS) * EXY + cen;
         float F[3];
         force_ring<R, NG, EX>(pz, p, F);
+        // a wait that gives up only marks the thread; the block leaves together
+        // at the next vote (computing on an incomplete stage meanwhile is
+        // harmless: every address stays in bounds)
+        const int cb = it & 1;
+        late |= !mbar_wait_bounded(&bar[1 + cb], (unsigned)((it - 2 * R) >> 1) & 1u);
+        const float *cs = cb ? cst1 : cst0;
+        float g[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            g[i] = cs[i * (TY * BOXW) + ty * BOXW + (tx + 4 - cvel<19>(i, 0))];
         float out[19];
         collide19(g, F, p, out);
         store19(B, p, xi, yi, zc, out);
@@ -208,7 +226,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
         // flight a bounded chance to land, and leave the step
         if (t == 0) {
             atomicAdd(&flags->timeouts, 1ULL);
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < 3; ++k) {
                 mbar_wait_bounded(&bar[k], 0u);
                 mbar_wait_bounded(&bar[k], 1u);
             }
@@ -221,7 +239,9 @@ __global__ void __launch_bounds__(TX * TY, 2)
 
 template <int R>
 constexpr int smem_bytes() {
-    return (2 * 19 * box_stride<R>() + (2 * R + 2) * (TX + 2 * R) * (TY + 2 * R)) * 4 + 16;
+    return (19 * box_stride<R>() + 2 * 19 * TY * BOXW + (2 * R + 2) * (TX + 2 * R) * (TY + 2 * R)) *
+               4 +
+           32;
 }
 
 }  // namespace ft
@@ -242,8 +262,10 @@ bool tma_make_maps(lb_ctx *c) {
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     for (int b = 0; b < 2; ++b)
-        for (int r = 0; r < 2; ++r) {
-            const int rows = fc::TY + 2 * (r + 1);   // psi-plane boxes, R = 1, 2
+        for (int r = 0; r < 3; ++r) {
+            // boxes of TY + 2R rows (psi planes, R = 1, 2) and TY rows
+            // (collision planes)
+            const int rows = r < 2 ? fc::TY + 2 * (r + 1) : fc::TY;
             cuuint64_t dims[3] = {(cuuint64_t)c->g.nxp, (cuuint64_t)c->g.nyp,
                                   (cuuint64_t)c->Q * c->g.nz};
             cuuint64_t strides[2] = {(cuuint64_t)c->g.nxp * 4,
@@ -278,15 +300,17 @@ cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng) {
     }
     const int sm1 = ft::smem_bytes<1>(), sm2 = ft::smem_bytes<2>();
     const CUtensorMap &m1 = c->tmap[c->cur][0], &m2 = c->tmap[c->cur][1];
+    const CUtensorMap &mc = c->tmap[c->cur][2];
+    (void)A;
     tm_begin(c, LB_KERNEL_FUSED);
     switch (ng) {
-        case 1: ft::k_fused3d_tma<1, 1><<<grid, block, sm1, c->stream>>>(m1, A, B, p, c->flags); break;
-        case 2: ft::k_fused3d_tma<1, 2><<<grid, block, sm1, c->stream>>>(m1, A, B, p, c->flags); break;
-        case 3: ft::k_fused3d_tma<1, 3><<<grid, block, sm1, c->stream>>>(m1, A, B, p, c->flags); break;
-        case 4: ft::k_fused3d_tma<2, 4><<<grid, block, sm2, c->stream>>>(m2, A, B, p, c->flags); break;
-        case 5: ft::k_fused3d_tma<2, 5><<<grid, block, sm2, c->stream>>>(m2, A, B, p, c->flags); break;
-        case 6: ft::k_fused3d_tma<2, 6><<<grid, block, sm2, c->stream>>>(m2, A, B, p, c->flags); break;
-        default: ft::k_fused3d_tma<2, 7><<<grid, block, sm2, c->stream>>>(m2, A, B, p, c->flags); break;
+        case 1: ft::k_fused3d_tma<1, 1><<<grid, block, sm1, c->stream>>>(m1, mc, B, p, c->flags); break;
+        case 2: ft::k_fused3d_tma<1, 2><<<grid, block, sm1, c->stream>>>(m1, mc, B, p, c->flags); break;
+        case 3: ft::k_fused3d_tma<1, 3><<<grid, block, sm1, c->stream>>>(m1, mc, B, p, c->flags); break;
+        case 4: ft::k_fused3d_tma<2, 4><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
+        case 5: ft::k_fused3d_tma<2, 5><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
+        case 6: ft::k_fused3d_tma<2, 6><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
+        default: ft::k_fused3d_tma<2, 7><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
     }
     tm_end(c);
     c->launches += 1;
