@@ -241,6 +241,46 @@ lb_status lb_timing(lb_ctx *ctx, int enable);
  * (launches[LB_KERNEL_KINDS]); either pointer may be NULL. */
 lb_status lb_timing_read(lb_ctx *ctx, double *ms, long long *launches);
 
+/* Largest lattice (nodes) lb_step_fp64_static accepts: 2^20, i.e. a fixed
+ * 8 MiB of device memory (plus 64 bytes of counters) per GPU. */
+#define LB_STATIC_MAX_NODES (1LL << 20)
+
+/* One binary64 step that allocates nothing.  This entry point has no
+ * counterpart in the paper; it exists for callers that cannot allocate device
+ * memory where they step a lattice -- code running under another framework's
+ * memory pool that forbids direct cudaMalloc, latency-critical loops where an
+ * allocation or the synchronisation it can imply is not acceptable, or
+ * embeddings that may only use buffers they already own.
+ *
+ * The caller owns both population buffers: f_in and f_out are device arrays
+ * [Q][N] float64 in the state layout of lb_get_state (post-streaming
+ * populations, x fastest); f_out receives the populations one step later.
+ * They must not overlap.  The stencil is given as the canonical pair list of
+ * lb_expand_stencil (n_pairs vectors of 3 ints in pair_vec and their weights
+ * in pair_w, host arrays).  lattice, nx, ny, nz, tau, G and g_convention mean
+ * what they mean in lb_params.  The arithmetic and rounding order are those
+ * of lb_step in LB_FP64 mode, so results are identical bit for bit.  Work is
+ * enqueued on cuda_stream (NULL: the legacy default stream) and the call
+ * returns without waiting.  No density check is reported.
+ *
+ * The only scratch, the lattice's psi field and a few counters, lives in one
+ * array of fixed size compiled into the library (LB_STATIC_MAX_NODES nodes):
+ * every GPU that loads the library holds it until the process exits.  The
+ * first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents: each call clears its counters and overwrites psi before
+ * use, but two calls that overlap on the GPU (different streams, or
+ * concurrent host threads) race on it and must be serialised by the caller.
+ *
+ * LB_EINVAL for bad arguments, for f_in == f_out, or for more than
+ * LB_STATIC_MAX_NODES nodes (with a message in lb_last_cuda_error);
+ * LB_ECUDA if a CUDA call fails. */
+lb_status lb_step_fp64_static(int lattice, int nx, int ny, int nz, double tau, double G,
+                              int g_convention, int n_pairs, const int *pair_vec,
+                              const double *pair_w, const double *f_in, double *f_out,
+                              void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,6 +82,9 @@ _SIGS = {
     "lb_kernel_launches": ([_vp], ctypes.c_longlong),
     "lb_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "lb_set_option": ([_vp, ctypes.c_int, ctypes.c_longlong], ctypes.c_int),
+    "lb_step_fp64_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                             _ip, _dp, _vp, _vp, _vp], ctypes.c_int),
     "lb_fused_active": ([_vp], ctypes.c_int),
     "lb_timing_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
 }
@@ -261,6 +264,23 @@ def lb_set_option(ctx, option, value):
 def lb_fused_active(ctx):
     """0: two-kernel path, 1: fused kernel (cp.async), 2: fused kernel (TMA)."""
     return int(_lib.lb_fused_active(_vp(ctx)))
+
+
+LB_STATIC_MAX_NODES = 1 << 20
+
+
+def lb_step_fp64_static(params, pair_vec, pair_w, f_in_ptr, f_out_ptr, stream=None):
+    """One binary64 step that allocates nothing (see sclbm.h).  f_in_ptr and
+    f_out_ptr are device addresses (e.g. ``tensor.data_ptr()``) of [Q][N]
+    float64 buffers the caller owns; pair_vec/pair_w come from
+    lb_expand_stencil.  Enqueued on ``stream`` (a cudaStream_t as int)."""
+    vec = np.ascontiguousarray(np.asarray(pair_vec, dtype=np.int32).reshape(-1, 3))
+    w = np.ascontiguousarray(np.asarray(pair_w, dtype=np.float64).ravel())
+    _check(_lib.lb_step_fp64_static(params.lattice, params.nx, params.ny, params.nz,
+                                    params.tau, params.G, params.g_convention, len(w),
+                                    vec.ctypes.data_as(_ip), _ptr(w), _vp(f_in_ptr),
+                                    _vp(f_out_ptr), _vp(stream) if stream else None),
+           "lb_step_fp64_static")
 
 
 LB_KERNEL_PSI, LB_KERNEL_COLLIDE, LB_KERNEL_FUSED, LB_KERNEL_OTHER = range(4)

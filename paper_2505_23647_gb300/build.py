@@ -26,6 +26,7 @@ UNITS = {
     "fp32.cu": [],
     "fused3d.cu": [],
     "fused3d_tma.cu": [],
+    "noalloc.cu": ["-fmad=false"],
 }
 
 

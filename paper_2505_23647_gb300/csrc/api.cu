@@ -225,6 +225,10 @@ lb_status check_flags(lb_ctx *c, Flags *h) {
 
 }  // namespace
 
+void lb_set_error_message(const char *msg) {
+    std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s", msg);
+}
+
 namespace sclbm {
 
 void tm_begin(lb_ctx *c, int kind) {

@@ -99,6 +99,9 @@ struct lb_ctx {
     long long kind_n[LB_KERNEL_KINDS];
 };
 
+// set the thread's last-error message returned by lb_last_cuda_error
+void lb_set_error_message(const char *msg);
+
 namespace sclbm {
 // per-kernel timing brackets (no-ops unless lb_timing is enabled)
 void tm_begin(lb_ctx *c, int kind);
