@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
         float F[3];
         force_ring<R, NG, EX>(pz, p, F);
         float out[19];
-        collide19(g, F, p, out);
+        collide19(g, dens(g), F, p, out);
         if (owner) store19(B, p, xi, yi, zc, out);
     }
     if (bad) atomicMin(&flags->err_step, flags->step);
@@ -195,13 +195,32 @@ bool fused3d_applicable(const lb_ctx *c, float *W, int *ng) {
 fc::Params fused_params(const lb_ctx *c, const float *W) {
     fc::Params p;
     for (int q = 0; q < 7; ++q) p.W[q] = W[q];
-    p.omega = (float)c->k.omega;
+    double M1 = 0.0, M2 = 0.0;
+    {   // plane-split force: weights summed over the in-plane rings k = 0,1,2,4,5
+        // at z offsets 1 and 2 (|e|^2 = k + d^2; groups 0..6 have |e|^2 = 1,2,3,4,5,6,8)
+        const double w[7] = {W[0], W[1], W[2], W[3], W[4], W[5], W[6]};
+        M1 = w[0] + 4.0 * w[1] + 4.0 * w[2] + 4.0 * w[4] + 8.0 * w[5];
+        M2 = 2.0 * (w[3] + 4.0 * w[4] + 4.0 * w[5] + 4.0 * w[6]);
+    }
+    for (int q = 0; q < 7; ++q) p.W2[q] = 2.f * W[q];
+    p.M1 = (float)M1;
+    p.M2 = (float)M2;
+    const double om = c->k.omega;
+    p.omega = (float)om;
+    p.keep = (float)(1.0 - om);
     p.mGp = (float)c->k.mGp;
     p.rho0 = (float)c->k.rho0;
     const double pref = 1.0 - 1.0 / (2.0 * c->p.tau);
-    p.cw[0] = (float)(pref / 3.0);
-    p.cw[1] = (float)(pref / 18.0);
-    p.cw[2] = (float)(pref / 36.0);
+    const double wc[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    for (int k = 0; k < 3; ++k) {
+        const double cw = pref * wc[k];
+        p.omw[k] = (float)(om * wc[k]);
+        p.m3cw[k] = (float)(-3.0 * cw);
+        p.b45[k] = (float)(4.5 * om * wc[k]);
+        p.d3[k] = (float)(3.0 * om * wc[k]);
+        p.c9[k] = (float)(9.0 * cw);
+        p.c3[k] = (float)(3.0 * cw);
+    }
     p.nx = c->g.nx;
     p.ny = c->g.ny;
     p.nz = c->g.nz;

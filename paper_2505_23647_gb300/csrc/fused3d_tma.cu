@@ -1,11 +1,17 @@
 // fused3d_tma.cu -- the fused single-pass D3Q19 step with TMA staging.
 //
-// Same model and schedule as fused3d.cu (32 x 8 column tiles marching z
-// chunks, psi ring of 2R+2 planes in shared memory, collision of plane zz-R
-// once psi of zz is known), but each plane's populations reach shared memory
-// through the Tensor Memory Accelerator: one cp.async.bulk.tensor per
-// population (19 per plane per CTA, issued by one thread and completed on an
-// mbarrier) instead of one 4-byte copy per population and node.
+// A CTA owns a 32 x 8 column tile and marches a chunk of z planes.  Each
+// plane's pulled populations A_i(x - xi_i) (tile plus a radius-R halo) reach
+// shared memory through the Tensor Memory Accelerator: one
+// cp.async.bulk.tensor per population (19 per plane, issued by one thread,
+// completed on an mbarrier) into a double-buffered stage, two planes ahead.
+// From the stage each thread forms n and psi = exp(-1/n) of its node (and of
+// a halo node) into a psi plane, keeping its node's 19 pulled populations in
+// registers.  The stencil force is accumulated plane by plane in registers
+// (plane_force: one pass over a psi plane serves every target plane within
+// R), so psi planes never stay in shared memory beyond one step of the
+// march; plane z - R is collided as soon as plane z has been added, from the
+// populations held since then.
 //
 // Layout: the population arrays carry periodic ghost columns (4 on each side
 // in x) and rows (3 on each side in y) around every x-y plane, so the box a
@@ -114,43 +120,25 @@ __device__ __forceinline__ float psi_from_boxes(const float *stage, int ex, int 
     return psi32(n);
 }
 
-// issue the 19 population boxes of the tile's collision plane zc (rows
-// y0 - c_y .. y0 + TY - c_y, the same 40 columns)
-__device__ __forceinline__ void issue_collision_plane(const CUtensorMap *map, float *stage,
-                                                      unsigned long long *bar, int zc, int x0,
-                                                      int y0, const Params &p) {
-    constexpr int BOX = TY * BOXW;
-    mbar_expect_tx(bar, 19u * BOX * 4u);
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const int cy = cvel<19>(i, 1), cz = cvel<19>(i, 2);
-        tma_load_3d(stage + i * BOX, map, x0 + p.ox - 4, y0 + p.oy - cy,
-                    i * p.nz + wrap1(zc - cz, p.nz), bar);
-    }
-}
-
-// Schedule of one CTA (it = 0 .. nit-1, zz = z0 - R + it, zc = zz - R):
-//   wait psi-stage(it); psi(zz) -> ring; barrier (+ timeout vote);
-//   thread 0 issues psi-stage(it+1) into the single psi stage (all reads of
-//   it are behind the barrier) and collision-stage(it+1) into buffer
-//   (it+1)&1 (its last reader, collision(it-1), is behind the barrier too);
-//   force(zc) from the ring; wait collision-stage(it); collide; store.
-// Both copies therefore overlap at least the force and collision phase of
-// the iteration before they are needed.
+// Schedule of one CTA (it = 0 .. nit-1, plane zz = z0 - R + it, stage it & 1):
+//   wait stage(it); pulled populations of the own node -> registers, psi of
+//   the own and the halo node -> psi plane (it & 1); barrier (+ timeout vote);
+//   thread 0 refills stage(it) with plane zz + 2 (its readers are all behind
+//   the barrier); add this plane's force contributions to the 2R+1 targets
+//   zz - R .. zz + R; collide target zz - R (complete now) and store it.
+// The psi plane (it & 1) is rewritten at it + 2, after every thread has
+// passed the barrier of it + 1, i.e. finished reading it.
 template <int R, int NG>
 __global__ void __launch_bounds__(TX * TY, 2)
-    k_fused3d_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap cmap,
-                  float *__restrict__ B, const Params p, Flags *flags) {
-    constexpr int EX = TX + 2 * R, EY = TY + 2 * R, NS = 2 * R + 2, EXY = EX * EY;
+    k_fused3d_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ B, const Params p,
+                  Flags *flags) {
+    constexpr int EX = TX + 2 * R, EY = TY + 2 * R, EXY = EX * EY;
     constexpr int HALO = EXY - TX * TY;
-    constexpr int STAGE = 19 * box_stride<R>();
-    constexpr int CSTAGE = 19 * TY * BOXW;
+    constexpr int BS = box_stride<R>(), STAGE = 19 * BS;
     extern __shared__ __align__(128) float smem[];
-    float *stage = smem;                          // psi plane: 19 boxes, tile + halo
-    float *cst0 = smem + STAGE;                   // collision plane, two buffers
-    float *cst1 = cst0 + CSTAGE;
-    float *ring = cst1 + CSTAGE;                  // NS planes of psi
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(ring + NS * EXY);
+    float *stage = smem;                          // two stages of 19 boxes
+    float *pbuf = smem + 2 * STAGE;               // two psi planes (tile + halo)
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(pbuf + 2 * EXY);
 
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -162,71 +150,101 @@ __global__ void __launch_bounds__(TX * TY, 2)
     if (has_halo) halo_coords<R>(t, hx, hy);
     const int cen = (ty + R) * EX + (tx + R);
     const int hof = hy * EX + hx;
+    const int own = (ty + R) * BOXW + tx + 4;    // own node in a box, before the x shift
     bool bad = false;
 
     if (t == 0) {
-        mbar_init(&bar[0], 1);   // psi stage full
-        mbar_init(&bar[1], 1);   // collision buffer 0 full
-        mbar_init(&bar[2], 1);   // collision buffer 1 full
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
     const int nit = (z1 - z0) + 2 * R;
-    if (t == 0) issue_plane<R>(&map, stage, &bar[0], wrap1(z0 - R, p.nz), x0, y0, p);
-    bool timed_out = false, late = false;
+    if (t == 0) {
+        issue_plane<R>(&map, stage, &bar[0], wrap1(z0 - R, p.nz), x0, y0, p);
+        issue_plane<R>(&map, stage + STAGE, &bar[1], wrap1(z0 - R + 1, p.nz), x0, y0, p);
+    }
+    float gq[R + 1][19];        // pulled populations of planes zz - R .. zz
+    float dq[R + 1];            // their shifted densities
+    float ps[2 * R + 1];        // own psi of planes zz - 2R .. zz
+    float acc[2 * R + 1][3];    // force sums of targets zz - R .. zz + R
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) acc[k][0] = acc[k][1] = acc[k][2] = ps[k] = 0.f;
+    bool timed_out = false;
     for (int it = 0; it < nit; ++it) {
-        const int zz = wrap1(z0 - R + it, p.nz);
-        // each thread's own wait makes the stage visible to it; the vote on
-        // a timed-out wait rides on the barrier that publishes psi
-        const bool ok = mbar_wait_bounded(&bar[0], (unsigned)it & 1u);
-        float *slot = ring + (it % NS) * EXY;
-        slot[cen] = psi_from_boxes<R>(stage, tx + R, ty + R, p.rho0, bad);
+        const int b = it & 1;
+        const bool ok = mbar_wait_bounded(&bar[b], (unsigned)(it >> 1) & 1u);
+        const float *st = stage + b * STAGE;
+        float *pb = pbuf + b * EXY;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) gq[R][i] = st[i * BS + own - cvel<19>(i, 0)];
+        dq[R] = dens(gq[R]);
+        {
+            const float n = dq[R] + p.rho0;
+            bad |= !(n > 0.f);
+            ps[2 * R] = psi32(n);
+        }
+        pb[cen] = ps[2 * R];
         if (has_halo) {
             bool dummy = false;
-            slot[hof] = psi_from_boxes<R>(stage, hx, hy, p.rho0, dummy);
+            pb[hof] = psi_from_boxes<R>(st, hx, hy, p.rho0, dummy);
         }
-        if (!__syncthreads_and(ok && !late)) {
+        if (!__syncthreads_and(ok)) {
             timed_out = true;
             break;
         }
-        if (t == 0) {
-            // the stages' previous readers are all behind the barrier above;
-            // order their generic-proxy reads before the async-proxy writes
+        if (t == 0 && it + 2 < nit) {
+            // the stage's readers are all behind the barrier above; order their
+            // generic-proxy reads before the async-proxy writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            if (it + 1 < nit)
-                issue_plane<R>(&map, stage, &bar[0], wrap1(zz + 1, p.nz), x0, y0, p);
-            if (it + 1 >= 2 * R && it + 1 < nit)
-                issue_collision_plane(&cmap, ((it + 1) & 1) ? cst1 : cst0, &bar[1 + ((it + 1) & 1)],
-                                      wrap1(zz + 1 - R, p.nz), x0, y0, p);
+            issue_plane<R>(&map, stage + b * STAGE, &bar[b], wrap1(z0 - R + it + 2, p.nz), x0, y0, p);
         }
-        if (it < 2 * R) continue;
-        // ---- collide plane zc = zz - R --------------------------------------
-        const int zc = wrap1(zz - R, p.nz);
-        const float *pz[2 * R + 1];
+        {   // this plane's share of the force on targets zz - R .. zz + R
+            float cx[R + 1], cy[R + 1], cz[R + 1];
+            plane_force<R, NG, EX>(pb + cen, ps[2 * R], p, cx, cy, cz);
 #pragma unroll
-        for (int k = -R; k <= R; ++k) pz[k + R] = ring + ((it - R + k + NS) % NS) * EXY + cen;
-        float F[3];
-        force_ring<R, NG, EX>(pz, p, F);
-        // a wait that gives up only marks the thread; the block leaves together
-        // at the next vote (computing on an incomplete stage meanwhile is
-        // harmless: every address stays in bounds)
-        const int cb = it & 1;
-        late |= !mbar_wait_bounded(&bar[1 + cb], (unsigned)((it - 2 * R) >> 1) & 1u);
-        const float *cs = cb ? cst1 : cst0;
-        float g[19];
+            for (int k = 0; k <= 2 * R; ++k) {
+                const int d = R - k, ad = d < 0 ? -d : d;   // plane offset from target
+                acc[k][0] += cx[ad];
+                acc[k][1] += cy[ad];
+                if (d > 0) acc[k][2] += cz[ad];
+                if (d < 0) acc[k][2] -= cz[ad];
+            }
+        }
+        if (it >= 2 * R) {   // collide plane zz - R
+            float F[3];
+            float fz = fmaf(p.M1, ps[R + 1] - ps[R - 1], acc[0][2]);
+            if constexpr (R >= 2) fz = fmaf(p.M2, ps[R + 2] - ps[R - 2], fz);
+            const float pre = p.mGp * ps[R];
+            F[0] = pre * acc[0][0];
+            F[1] = pre * acc[0][1];
+            F[2] = pre * fz;
+            float out[19];
+            collide19(gq[0], dq[0], F, p, out);
+            store19(B, p, xi, yi, wrap1(z0 - R + it - R, p.nz), out);
+        }
+        // advance the register windows by one plane
 #pragma unroll
-        for (int i = 0; i < 19; ++i)
-            g[i] = cs[i * (TY * BOXW) + ty * BOXW + (tx + 4 - cvel<19>(i, 0))];
-        float out[19];
-        collide19(g, F, p, out);
-        store19(B, p, xi, yi, zc, out);
+        for (int k = 0; k < 2 * R; ++k) {
+            acc[k][0] = acc[k + 1][0];
+            acc[k][1] = acc[k + 1][1];
+            acc[k][2] = acc[k + 1][2];
+            ps[k] = ps[k + 1];
+        }
+        acc[2 * R][0] = acc[2 * R][1] = acc[2 * R][2] = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            dq[r] = dq[r + 1];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) gq[r][i] = gq[r + 1][i];
+        }
     }
-    if (__syncthreads_or(timed_out || late)) {
-        // a barrier gave up (never expected): record it, give copies still in
+    if (__syncthreads_or(timed_out)) {
+        // a wait gave up (never expected): record it, give copies still in
         // flight a bounded chance to land, and leave the step
         if (t == 0) {
             atomicAdd(&flags->timeouts, 1ULL);
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < 2; ++k) {
                 mbar_wait_bounded(&bar[k], 0u);
                 mbar_wait_bounded(&bar[k], 1u);
             }
@@ -239,9 +257,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
 
 template <int R>
 constexpr int smem_bytes() {
-    return (19 * box_stride<R>() + 2 * 19 * TY * BOXW + (2 * R + 2) * (TX + 2 * R) * (TY + 2 * R)) *
-               4 +
-           32;
+    return (2 * 19 * box_stride<R>() + 2 * (TX + 2 * R) * (TY + 2 * R)) * 4 + 16;
 }
 
 }  // namespace ft
@@ -262,10 +278,9 @@ bool tma_make_maps(lb_ctx *c) {
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     for (int b = 0; b < 2; ++b)
-        for (int r = 0; r < 3; ++r) {
-            // boxes of TY + 2R rows (psi planes, R = 1, 2) and TY rows
-            // (collision planes)
-            const int rows = r < 2 ? fc::TY + 2 * (r + 1) : fc::TY;
+        for (int r = 0; r < 2; ++r) {
+            // boxes of TY + 2R rows (R = 1, 2)
+            const int rows = fc::TY + 2 * (r + 1);
             cuuint64_t dims[3] = {(cuuint64_t)c->g.nxp, (cuuint64_t)c->g.nyp,
                                   (cuuint64_t)c->Q * c->g.nz};
             cuuint64_t strides[2] = {(cuuint64_t)c->g.nxp * 4,
@@ -285,7 +300,6 @@ cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng) {
     fc::Params p = fused_params(c, W);
     dim3 block(fc::TX, fc::TY);
     dim3 grid(c->g.nx / fc::TX, c->g.ny / fc::TY, (c->g.nz + p.zchunk - 1) / p.zchunk);
-    const float *A = (const float *)c->f[c->cur];
     float *B = (float *)c->f[1 - c->cur];
     static bool attr_done = false;
     if (!attr_done) {
@@ -300,17 +314,15 @@ cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng) {
     }
     const int sm1 = ft::smem_bytes<1>(), sm2 = ft::smem_bytes<2>();
     const CUtensorMap &m1 = c->tmap[c->cur][0], &m2 = c->tmap[c->cur][1];
-    const CUtensorMap &mc = c->tmap[c->cur][2];
-    (void)A;
     tm_begin(c, LB_KERNEL_FUSED);
     switch (ng) {
-        case 1: ft::k_fused3d_tma<1, 1><<<grid, block, sm1, c->stream>>>(m1, mc, B, p, c->flags); break;
-        case 2: ft::k_fused3d_tma<1, 2><<<grid, block, sm1, c->stream>>>(m1, mc, B, p, c->flags); break;
-        case 3: ft::k_fused3d_tma<1, 3><<<grid, block, sm1, c->stream>>>(m1, mc, B, p, c->flags); break;
-        case 4: ft::k_fused3d_tma<2, 4><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
-        case 5: ft::k_fused3d_tma<2, 5><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
-        case 6: ft::k_fused3d_tma<2, 6><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
-        default: ft::k_fused3d_tma<2, 7><<<grid, block, sm2, c->stream>>>(m2, mc, B, p, c->flags); break;
+        case 1: ft::k_fused3d_tma<1, 1><<<grid, block, sm1, c->stream>>>(m1, B, p, c->flags); break;
+        case 2: ft::k_fused3d_tma<1, 2><<<grid, block, sm1, c->stream>>>(m1, B, p, c->flags); break;
+        case 3: ft::k_fused3d_tma<1, 3><<<grid, block, sm1, c->stream>>>(m1, B, p, c->flags); break;
+        case 4: ft::k_fused3d_tma<2, 4><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
+        case 5: ft::k_fused3d_tma<2, 5><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
+        case 6: ft::k_fused3d_tma<2, 6><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
+        default: ft::k_fused3d_tma<2, 7><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
     }
     tm_end(c);
     c->launches += 1;

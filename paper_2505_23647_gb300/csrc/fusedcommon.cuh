@@ -36,10 +36,15 @@ __host__ __device__ constexpr int group_end(int g) {
 
 struct Params {
     float W[7];      // group weights (0 for groups the stencil lacks)
+    float W2[7];     // 2 W
+    float M1, M2;    // z-offset sums of weights (plane-split force; M2 doubled)
     float omega;     // 1/tau
+    float keep;      // 1 - 1/tau
     float mGp;       // -G'
     float rho0;      // population shift
-    float cw[3];     // (1 - 1/(2 tau)) w for |xi|^2 = 0, 1, 2
+    // collision constants per velocity class |xi|^2 = 0, 1, 2 (weight w,
+    // cw = (1 - 1/(2 tau)) w): omega w, -3 cw, 4.5 omega w, 3 omega w, 9 cw, 3 cw
+    float omw[3], m3cw[3], b45[3], d3[3], c9[3], c3[3];
     int nx, ny, nz;  // lattice
     int nxp, nyp;    // padded population plane
     int ox, oy;      // node (0,0) inside a padded plane
@@ -83,49 +88,137 @@ __device__ __forceinline__ void force_ring(const float *const *pz, const Params 
     F[2] *= pre;
 }
 
-// BGK + Guo of one node in shifted binary32 (eqs. f_eq, GuoForcing, omega_i):
-// equilibrium and source split into parts even and odd in xi, one
-// evaluation per pair of opposite velocities (i, i+1).
-__device__ __forceinline__ void collide19(const float *g, const float *F, const Params &p,
+// group index of |e|^2 = s among the seven E8 groups (-1: no group)
+__host__ __device__ constexpr int group_of_sq(int s) {
+    return s == 1 ? 0 : s == 2 ? 1 : s == 3 ? 2 : s == 4 ? 3 : s == 5 ? 4 : s == 6 ? 5 : s == 8 ? 6 : -1;
+}
+
+// acc += W(s) v (or 2 W(s) v) when the group of |e|^2 = s is among the first NG
+template <int NG, int S, bool TWICE = false>
+__device__ __forceinline__ void wfma(float &acc, const Params &p, float v) {
+    constexpr int q = group_of_sq(S);
+    if constexpr (q >= 0 && q < NG) acc = fmaf(TWICE ? p.W2[q] : p.W[q], v, acc);
+}
+
+// Plane-split form of the stencil force (eq. sc_f).  Grouping the vectors e
+// by their z component d and in-plane ring k = e_x^2 + e_y^2, one plane of
+// psi at z offset d from the target contributes
+//   F_x += sum_k W(k + d^2) X_k,  F_y += sum_k W(k + d^2) Y_k,
+//   F_z += d sum_k W(k + d^2) S_k,
+// with X_k, Y_k, S_k the sums of e_x psi, e_y psi, psi over the ring.  One
+// pass over a plane serves all 2R+1 targets it touches; the sums X_k, Y_k,
+// cz of a plane depend on |d| only.  S_k is taken relative to the column's
+// own psi0 (differences of nearby values are exact in binary32); the psi0
+// part, sum_d d M_|d| psi0(z + d), is added at the target from its own
+// column (M1, M2 are those weight sums, M2 doubled).
+//   pc : this column's psi in a plane of rows EX apart; s0 = *pc
+//   cx[d], cy[d] : in-plane parts for |d| = 0..R;  cz[d] : |d| (sum W S^) for d >= 1
+template <int R, int NG, int EX>
+__device__ __forceinline__ void plane_force(const float *pc, float s0, const Params &p, float *cx,
+                                            float *cy, float *cz) {
+    auto q = [&](int dx, int dy) { return pc[dy * EX + dx] - s0; };
+    // ring k = 1
+    const float e = q(1, 0), w = q(-1, 0), nn = q(0, 1), ss = q(0, -1);
+    const float X1 = e - w, Y1 = nn - ss, S1 = (e + w) + (nn + ss);
+    // ring k = 2
+    const float a = q(1, 1), b = q(1, -1), c = q(-1, 1), d = q(-1, -1);
+    const float ab = a + b, cd = c + d, ac = a + c, bd = b + d;
+    const float X2 = ab - cd, Y2 = ac - bd, S2 = ab + cd;
+#pragma unroll
+    for (int k = 0; k <= R; ++k) cx[k] = cy[k] = cz[k] = 0.f;
+    wfma<NG, 1>(cx[0], p, X1);
+    wfma<NG, 2>(cx[0], p, X2);
+    wfma<NG, 1>(cy[0], p, Y1);
+    wfma<NG, 2>(cy[0], p, Y2);
+    wfma<NG, 2>(cx[1], p, X1);
+    wfma<NG, 3>(cx[1], p, X2);
+    wfma<NG, 2>(cy[1], p, Y1);
+    wfma<NG, 3>(cy[1], p, Y2);
+    wfma<NG, 2>(cz[1], p, S1);
+    wfma<NG, 3>(cz[1], p, S2);
+    if constexpr (R >= 2) {
+        // ring k = 4 (X, Y halved: e_x = +-2)
+        const float e2 = q(2, 0), w2 = q(-2, 0), n2 = q(0, 2), s2 = q(0, -2);
+        const float X4h = e2 - w2, Y4h = n2 - s2, S4 = (e2 + w2) + (n2 + s2);
+        // ring k = 5: (+-2, +-1) and (+-1, +-2)
+        const float r21 = q(2, 1), r2m = q(2, -1), rm21 = q(-2, 1), rm2m = q(-2, -1);
+        const float r12 = q(1, 2), rm12 = q(-1, 2), r1m2 = q(1, -2), rm1m2 = q(-1, -2);
+        const float A = r21 + r2m, B = rm21 + rm2m, C = r12 + r1m2, D = rm12 + rm1m2;
+        const float E = r21 + rm21, Fv = r2m + rm2m, G = r12 + rm12, H = r1m2 + rm1m2;
+        const float X5 = fmaf(2.f, A - B, C - D), Y5 = fmaf(2.f, G - H, E - Fv);
+        const float S5 = (A + B) + (C + D);
+        // ring k = 8 (halved), raw values
+        const float k1 = pc[2 * EX + 2], k2 = pc[-2 * EX + 2], k3 = pc[2 * EX - 2], k4 = pc[-2 * EX - 2];
+        const float X8h = (k1 + k2) - (k3 + k4), Y8h = (k1 + k3) - (k2 + k4);
+        wfma<NG, 4, true>(cx[0], p, X4h);
+        wfma<NG, 5>(cx[0], p, X5);
+        wfma<NG, 8, true>(cx[0], p, X8h);
+        wfma<NG, 4, true>(cy[0], p, Y4h);
+        wfma<NG, 5>(cy[0], p, Y5);
+        wfma<NG, 8, true>(cy[0], p, Y8h);
+        wfma<NG, 5, true>(cx[1], p, X4h);
+        wfma<NG, 6>(cx[1], p, X5);
+        wfma<NG, 5, true>(cy[1], p, Y4h);
+        wfma<NG, 6>(cy[1], p, Y5);
+        wfma<NG, 5>(cz[1], p, S4);
+        wfma<NG, 6>(cz[1], p, S5);
+        wfma<NG, 5>(cx[2], p, X1);
+        wfma<NG, 6>(cx[2], p, X2);
+        wfma<NG, 8, true>(cx[2], p, X4h);
+        wfma<NG, 5>(cy[2], p, Y1);
+        wfma<NG, 6>(cy[2], p, Y2);
+        wfma<NG, 8, true>(cy[2], p, Y4h);
+        wfma<NG, 5, true>(cz[2], p, S1);
+        wfma<NG, 6, true>(cz[2], p, S2);
+        wfma<NG, 8, true>(cz[2], p, S4);
+    }
+}
+
+// BGK + Guo of one node in shifted binary32 (eqs. f_eq, GuoForcing, omega_i).
+// With u = (j + F/2)/n and base = dn - 1.5 n u.u (dn = n - rho0), a velocity
+// class of weight w and forcing weight cw = (1 - 1/(2 tau)) w gives each pair
+// of opposite velocities (xi, -xi)
+//   even part  E = omega w (base + 4.5 n (xi.u)^2) + cw (9 (xi.u)(xi.F) - 3 u.F)
+//   odd part   O = 3 omega w n (xi.u) + 3 cw (xi.F)
+// and out(xi) = (1 - omega) g(xi) + E + O, out(-xi) = (1 - omega) g(-xi) + E - O.
+__device__ __forceinline__ void collide19(const float *g, float dn, const float *F, const Params &p,
                                           float *out) {
-    const float dn = dens(g);
     const float n = dn + p.rho0;
     const float inv = __frcp_rn(n);
-    const float jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
-    const float jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
-    const float jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
+    const float d1 = g[1] - g[2], d3 = g[3] - g[4], d5 = g[5] - g[6];
+    const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12];
+    const float d13 = g[13] - g[14], d15 = g[15] - g[16], d17 = g[17] - g[18];
+    const float jx = ((d1 + d7) + (d9 + d11)) + d13;
+    const float jy = ((d3 + d7) + (d15 - d9)) + d17;
+    const float jz = ((d5 + d11) + (d15 - d13)) - d17;
     const float ux = fmaf(0.5f, F[0], jx) * inv;
     const float uy = fmaf(0.5f, F[1], jy) * inv;
     const float uz = fmaf(0.5f, F[2], jz) * inv;
     const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
     const float uF = fmaf(ux, F[0], fmaf(uy, F[1], uz * F[2]));
-    const float om = p.omega, keep = 1.f - p.omega;
-    const float w0 = 1.f / 3.f, w1 = 1.f / 18.f, w2 = 1.f / 36.f;
-    {   // rest population: g_eq = w0 (dn - 1.5 n uu), S = cw0 (-3 uF)
-        const float geq = w0 * fmaf(-1.5f * n, uu, dn);
-        out[0] = fmaf(keep, g[0], fmaf(om, geq, p.cw[0] * (-3.f * uF)));
-    }
-    const float base1 = fmaf(-1.5f * n, uu, dn);   // dn - 1.5 n uu
-    const float nb = 4.5f * n;
-#define SCLBM_PAIR(I, W, CW, CU, CF)                                            \
+    const float base = fmaf(-1.5f * n, uu, dn);
+    out[0] = fmaf(p.keep, g[0], fmaf(p.omw[0], base, p.m3cw[0] * uF));
+    const float a1 = fmaf(p.omw[1], base, p.m3cw[1] * uF);
+    const float a2 = fmaf(p.omw[2], base, p.m3cw[2] * uF);
+    const float b1 = p.b45[1] * n, b2 = p.b45[2] * n;
+    const float e1 = p.d3[1] * n, e2 = p.d3[2] * n;
+#define SCLBM_PAIR(I, C, CU, CF)                                                \
     {                                                                           \
         const float cu = (CU), cF = (CF);                                       \
-        const float ev = (W) * fmaf(nb * cu, cu, base1);                        \
-        const float od = (W) * (3.f * n) * cu;                                  \
-        const float sev = (CW) * fmaf(9.f * cu, cF, -3.f * uF);                 \
-        const float sod = (CW) * 3.f * cF;                                      \
-        out[I] = fmaf(keep, g[I], fmaf(om, ev + od, sev + sod));                \
-        out[I + 1] = fmaf(keep, g[I + 1], fmaf(om, ev - od, sev - sod));        \
+        const float ev = fmaf(cu, fmaf(b##C, cu, p.c9[C] * cF), a##C);          \
+        const float od = fmaf(e##C, cu, p.c3[C] * cF);                          \
+        out[I] = fmaf(p.keep, g[I], ev + od);                                   \
+        out[I + 1] = fmaf(p.keep, g[I + 1], ev - od);                           \
     }
-    SCLBM_PAIR(1, w1, p.cw[1], ux, F[0])
-    SCLBM_PAIR(3, w1, p.cw[1], uy, F[1])
-    SCLBM_PAIR(5, w1, p.cw[1], uz, F[2])
-    SCLBM_PAIR(7, w2, p.cw[2], ux + uy, F[0] + F[1])
-    SCLBM_PAIR(9, w2, p.cw[2], ux - uy, F[0] - F[1])
-    SCLBM_PAIR(11, w2, p.cw[2], ux + uz, F[0] + F[2])
-    SCLBM_PAIR(13, w2, p.cw[2], ux - uz, F[0] - F[2])
-    SCLBM_PAIR(15, w2, p.cw[2], uy + uz, F[1] + F[2])
-    SCLBM_PAIR(17, w2, p.cw[2], uy - uz, F[1] - F[2])
+    SCLBM_PAIR(1, 1, ux, F[0])
+    SCLBM_PAIR(3, 1, uy, F[1])
+    SCLBM_PAIR(5, 1, uz, F[2])
+    SCLBM_PAIR(7, 2, ux + uy, F[0] + F[1])
+    SCLBM_PAIR(9, 2, ux - uy, F[0] - F[1])
+    SCLBM_PAIR(11, 2, ux + uz, F[0] + F[2])
+    SCLBM_PAIR(13, 2, ux - uz, F[0] - F[2])
+    SCLBM_PAIR(15, 2, uy + uz, F[1] + F[2])
+    SCLBM_PAIR(17, 2, uy - uz, F[1] - F[2])
 #undef SCLBM_PAIR
 }
 

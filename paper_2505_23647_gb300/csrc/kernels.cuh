@@ -221,7 +221,6 @@ __global__ void __launch_bounds__(256) k_collide(const T *__restrict__ A, T *__r
         for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
         T fo[Q];
         collide<T, D, Q, SHIFT>(fi, n, dn, F, k, fo, nullptr, nullptr);
-#pragma unroll
         const long long ps = popidx(g, x, y, z);
 #pragma unroll
         for (int i = 0; i < Q; ++i) B[(long long)i * g.Np + ps] = fo[i];
