@@ -230,7 +230,7 @@ fc::Params fused_params(const lb_ctx *c, const float *W) {
     p.oy = c->g.oy;
     p.pplane = c->g.nxp * c->g.nyp;
     p.Np = (int)c->g.Np;
-    p.zchunk = c->fused_zchunk > 0 ? c->fused_zchunk : 32;
+    p.zchunk = c->fused_zchunk > 0 ? c->fused_zchunk : 16;
     return p;
 }
 

@@ -123,9 +123,9 @@ __device__ __forceinline__ float psi_from_boxes(const float *stage, int ex, int 
 // Schedule of one CTA (it = 0 .. nit-1, plane zz = z0 - R + it, stage it & 1):
 //   wait stage(it); pulled populations of the own node -> registers, psi of
 //   the own and the halo node -> psi plane (it & 1); barrier (+ timeout vote);
-//   thread 0 refills stage(it) with plane zz + 2 (its readers are all behind
-//   the barrier); add this plane's force contributions to the 2R+1 targets
-//   zz - R .. zz + R; collide target zz - R (complete now) and store it.
+//   the last thread refills stage(it) with plane zz + 2 (its readers are all
+//   behind the barrier); add this plane's force contributions to the 2R+1
+//   targets zz - R .. zz + R; collide target zz - R (complete now), store it.
 // The psi plane (it & 1) is rewritten at it + 2, after every thread has
 // passed the barrier of it + 1, i.e. finished reading it.
 template <int R, int NG>
@@ -133,8 +133,10 @@ __global__ void __launch_bounds__(TX * TY, 2)
     k_fused3d_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ B, const Params p,
                   Flags *flags) {
     constexpr int EX = TX + 2 * R, EY = TY + 2 * R, EXY = EX * EY;
-    constexpr int HALO = EXY - TX * TY;
+    constexpr int HALO = EXY - TX * TY, HALO_WARPS = (HALO + 31) / 32;
     constexpr int BS = box_stride<R>(), STAGE = 19 * BS;
+    constexpr int ISSUER = TX * TY - 1;           // a thread of a warp without halo work
+    static_assert(HALO_WARPS < TX * TY / 32, "the issuing warp must have no halo node");
     extern __shared__ __align__(128) float smem[];
     float *stage = smem;                          // two stages of 19 boxes
     float *pbuf = smem + 2 * STAGE;               // two psi planes (tile + halo)
@@ -145,22 +147,24 @@ __global__ void __launch_bounds__(TX * TY, 2)
     const int z0 = blockIdx.z * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int xi = x0 + tx, yi = y0 + ty;
+    const bool halo_warp = (t >> 5) < HALO_WARPS;   // warp-uniform
     int hx = 0, hy = 0;
+    if (halo_warp) halo_coords<R>(min(t, HALO - 1), hx, hy);
     const bool has_halo = t < HALO;
-    if (has_halo) halo_coords<R>(t, hx, hy);
     const int cen = (ty + R) * EX + (tx + R);
     const int hof = hy * EX + hx;
-    const int own = (ty + R) * BOXW + tx + 4;    // own node in a box, before the x shift
+    const int own = (ty + R) * BOXW + tx + 4;     // own node in a box, before the x shift
+    const int hbx = hy * BOXW + hx + 4 - R;       // halo node in a box, before the x shift
     bool bad = false;
 
-    if (t == 0) {
+    if (t == ISSUER) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
     const int nit = (z1 - z0) + 2 * R;
-    if (t == 0) {
+    if (t == ISSUER) {
         issue_plane<R>(&map, stage, &bar[0], wrap1(z0 - R, p.nz), x0, y0, p);
         issue_plane<R>(&map, stage + STAGE, &bar[1], wrap1(z0 - R + 1, p.nz), x0, y0, p);
     }
@@ -171,29 +175,39 @@ __global__ void __launch_bounds__(TX * TY, 2)
 #pragma unroll
     for (int k = 0; k <= 2 * R; ++k) acc[k][0] = acc[k][1] = acc[k][2] = ps[k] = 0.f;
     bool timed_out = false;
+
     for (int it = 0; it < nit; ++it) {
+        constexpr int PH = R, CS = 0;             // slots of planes zz and zz - R
         const int b = it & 1;
         const bool ok = mbar_wait_bounded(&bar[b], (unsigned)(it >> 1) & 1u);
         const float *st = stage + b * STAGE;
         float *pb = pbuf + b * EXY;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) gq[R][i] = st[i * BS + own - cvel<19>(i, 0)];
-        dq[R] = dens(gq[R]);
-        {
-            const float n = dq[R] + p.rho0;
+        for (int i = 0; i < 19; ++i) gq[PH][i] = st[i * BS + own - cvel<19>(i, 0)];
+        if (halo_warp) {
+            // the halo node's chain interleaves with the own node's
+            float gh[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) gh[i] = st[i * BS + hbx - cvel<19>(i, 0)];
+            dq[PH] = dens(gq[PH]);
+            const float n = dq[PH] + p.rho0, nh = dens(gh) + p.rho0;
             bad |= !(n > 0.f);
             ps[2 * R] = psi32(n);
-        }
-        pb[cen] = ps[2 * R];
-        if (has_halo) {
-            bool dummy = false;
-            pb[hof] = psi_from_boxes<R>(st, hx, hy, p.rho0, dummy);
+            const float psh = psi32(nh);
+            pb[cen] = ps[2 * R];
+            if (has_halo) pb[hof] = psh;
+        } else {
+            dq[PH] = dens(gq[PH]);
+            const float n = dq[PH] + p.rho0;
+            bad |= !(n > 0.f);
+            ps[2 * R] = psi32(n);
+            pb[cen] = ps[2 * R];
         }
         if (!__syncthreads_and(ok)) {
             timed_out = true;
             break;
         }
-        if (t == 0 && it + 2 < nit) {
+        if (t == ISSUER && it + 2 < nit) {
             // the stage's readers are all behind the barrier above; order their
             // generic-proxy reads before the async-proxy writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -220,10 +234,10 @@ __global__ void __launch_bounds__(TX * TY, 2)
             F[1] = pre * acc[0][1];
             F[2] = pre * fz;
             float out[19];
-            collide19(gq[0], dq[0], F, p, out);
-            store19(B, p, xi, yi, wrap1(z0 - R + it - R, p.nz), out);
+            collide19(gq[CS], dq[CS], F, p, out);
+            store19(B, p, xi, yi, z0 - 2 * R + it, out);
         }
-        // advance the register windows by one plane
+        // advance the force and psi windows by one plane
 #pragma unroll
         for (int k = 0; k < 2 * R; ++k) {
             acc[k][0] = acc[k + 1][0];
@@ -242,7 +256,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
     if (__syncthreads_or(timed_out)) {
         // a wait gave up (never expected): record it, give copies still in
         // flight a bounded chance to land, and leave the step
-        if (t == 0) {
+        if (t == ISSUER) {
             atomicAdd(&flags->timeouts, 1ULL);
             for (int k = 0; k < 2; ++k) {
                 mbar_wait_bounded(&bar[k], 0u);
