@@ -382,10 +382,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    global NX, NY, NZ, RADIUS
+    global NX, NY, NZ, RADIUS, WORKLOAD
     if args.size != 256:
         NX = NY = NZ = args.size
         RADIUS = 40.0 * args.size / 256.0
+        WORKLOAD = WORKLOAD.replace("256^3", f"{NX}^3 (profiling size)").replace(
+            "R=40", f"R={RADIUS:g}")
     dist, rank, ws = _dist()
     try:
         if args.impl == "reference":
