@@ -156,6 +156,13 @@ def reduce_max(dist, value, device=None):
     return float(t.item())
 
 
+def job_throughput(dist, ms, nodes, steps, ws, device=None):
+    """Whole-job MLUPS of N replicas: every rank updated `nodes` nodes for
+    `steps` steps; the job took the slowest rank's time (ms, max over ranks)."""
+    ms_max = reduce_max(dist, ms, device)
+    return ms_max, nodes * steps * ws / (ms_max * 1e3)
+
+
 def _workload_rho():
     import lbinputs as L
     return L.tanh_sphere(NX, NY, NZ, RADIUS, 0.15, 1.9, 2.0)
@@ -262,8 +269,7 @@ def run_gb300(args, dist, rank, ws):
     P.lb_timing(lat.ctx, 0)
     launches = lat.launches() - launches0
     stable = lat.sync() == P.LB_OK
-    ms_max = reduce_max(dist, ms, dev)
-    value = N * args.steps * ws / (ms_max * 1e3)
+    ms_max, value = job_throughput(dist, ms, N, args.steps, ws, dev)
 
     # dominant kernel of the step and its roofline
     kind = max((k for k in kt if kt[k][1]), key=lambda k: kt[k][0])
