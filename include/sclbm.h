@@ -223,8 +223,10 @@ enum {
 /* Set an option of the context.  LB_EINVAL for an unknown option or value. */
 lb_status lb_set_option(lb_ctx *ctx, int option, long long value);
 
-/* 0 if lb_step runs the two-kernel path, 1 the fused single-pass kernel
- * with cp.async staging, 2 the fused kernel with TMA staging. */
+/* 0 if lb_step runs the two-kernel path, 1 the fused single-pass D3Q19
+ * kernel with cp.async staging, 2 the fused D3Q19 kernel with TMA staging,
+ * 3 the fused single-pass D2Q9 kernel (shifted FP32, stencils on the 2D
+ * groups up to (2,2)). */
 int lb_fused_active(const lb_ctx *ctx);
 
 /* Kernel kinds of the step, for lb_timing_read. */
@@ -240,6 +242,53 @@ lb_status lb_timing(lb_ctx *ctx, int enable);
  * in milliseconds (ms[LB_KERNEL_KINDS]) and the number of launches timed
  * (launches[LB_KERNEL_KINDS]); either pointer may be NULL. */
 lb_status lb_timing_read(lb_ctx *ctx, double *ms, long long *launches);
+
+/* ---- batches of independent 2D lattices ------------------------------------
+ *
+ * The droplet and bubble runs of a Laplace / Tolman fit (Sec. V B) are many
+ * independent lattices of uneven size.  A batch steps them together: one
+ * launch per step covers every tile of every member (a grid of resident CTAs
+ * walking one tile table), and lb_batch_step replays a CUDA graph of 64 such
+ * launches.  Results are those of lb_step on each member (the same fused
+ * D2Q9 kernel), whatever the tile shape.
+ *
+ * Members are contexts created by lb_create: D2Q9, LB_FP32_SHIFTED, stencil
+ * set, every group among (1,0), (1,1), (2,0), (2,1), (2,2) (E4, E6, E8 and
+ * their tuned variants); LB_EUNSUPPORTED otherwise, LB_ESTATE if a stencil
+ * is missing, LB_EINVAL for a repeated or NULL member.  The batch borrows
+ * the members (their buffers, counters and host step counts advance with
+ * lb_batch_step); destroy the batch before any member.  A member may still
+ * be used on its own between batch calls: lb_batch_step orders itself after
+ * the work already queued on every member's stream, and the members' later
+ * work after it.  cuda_stream (NULL: a stream of the batch's own) carries the
+ * batch's launches. */
+typedef struct lb_batch lb_batch;
+
+lb_status lb_batch_create(lb_ctx *const *ctxs, int n, void *cuda_stream, lb_batch **out);
+lb_status lb_batch_destroy(lb_batch *batch);
+
+/* Advance every member by nsteps (asynchronous). */
+lb_status lb_batch_step(lb_batch *batch, int nsteps);
+
+/* Wait for the batch and check every member as lb_sync does; returns the
+ * first member status that is not LB_OK. */
+lb_status lb_batch_sync(lb_batch *batch);
+
+/* Kernel launches lb_batch_step has issued (one per step). */
+long long lb_batch_launches(const lb_batch *batch);
+
+/* Tile shapes: lb_batch_tile_count() candidates, index -> (tx, ty) nodes. */
+int lb_batch_tile_count(void);
+lb_status lb_batch_tile_shape(int index, int *tx, int *ty);
+lb_status lb_batch_set_tile(lb_batch *batch, int index);
+int lb_batch_get_tile(const lb_batch *batch);
+
+/* Autotuner: time steps_per_trial steps (rounded down to even, >= 2) with
+ * every tile shape, keep the fastest.  The members' states and counters are
+ * saved first and restored after each trial, so tuning does not advance the
+ * simulation.  ms_out (NULL or lb_batch_tile_count() doubles) receives the
+ * trial times.  Synchronous; allocates a copy of every member's state. */
+lb_status lb_batch_tune(lb_batch *batch, int steps_per_trial, double *ms_out);
 
 /* Largest lattice (nodes) lb_step_fp64_static accepts: 2^20, i.e. a fixed
  * 8 MiB of device memory (plus 64 bytes of counters) per GPU. */

@@ -87,6 +87,17 @@ _SIGS = {
                              _ip, _dp, _vp, _vp, _vp], ctypes.c_int),
     "lb_fused_active": ([_vp], ctypes.c_int),
     "lb_timing_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "lb_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(_vp)],
+                        ctypes.c_int),
+    "lb_batch_destroy": ([_vp], ctypes.c_int),
+    "lb_batch_step": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lb_batch_sync": ([_vp], ctypes.c_int),
+    "lb_batch_launches": ([_vp], ctypes.c_longlong),
+    "lb_batch_tile_count": ([], ctypes.c_int),
+    "lb_batch_tile_shape": ([ctypes.c_int, _ip, _ip], ctypes.c_int),
+    "lb_batch_set_tile": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lb_batch_get_tile": ([_vp], ctypes.c_int),
+    "lb_batch_tune": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -262,8 +273,65 @@ def lb_set_option(ctx, option, value):
 
 
 def lb_fused_active(ctx):
-    """0: two-kernel path, 1: fused kernel (cp.async), 2: fused kernel (TMA)."""
+    """0: two-kernel path, 1: fused D3Q19 kernel (cp.async), 2: fused D3Q19
+    kernel (TMA), 3: fused D2Q9 kernel."""
     return int(_lib.lb_fused_active(_vp(ctx)))
+
+
+def lb_batch_tile_shapes():
+    """The candidate tile shapes (tx, ty) of batches, by index."""
+    out = []
+    for i in range(_lib.lb_batch_tile_count()):
+        tx, ty = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.lb_batch_tile_shape(i, ctypes.byref(tx), ctypes.byref(ty)), "lb_batch_tile_shape")
+        out.append((tx.value, ty.value))
+    return out
+
+
+class Batch:
+    """Many D2Q9 shifted-FP32 lattices stepped by one launch per step
+    (``lb_batch_*``).  ``lattices`` are :class:`Lattice` objects (kept alive
+    by the batch); destroy the batch before them."""
+
+    def __init__(self, lattices, stream=None):
+        self.members = list(lattices)
+        arr = (_vp * len(self.members))(*[m.ctx for m in self.members])
+        out = _vp()
+        _check(_lib.lb_batch_create(arr, len(self.members), _vp(stream) if stream else None,
+                                    ctypes.byref(out)), "lb_batch_create")
+        self.b = out.value
+
+    def step(self, n=1):
+        _check(_lib.lb_batch_step(_vp(self.b), int(n)), "lb_batch_step")
+
+    def sync(self):
+        return _lib.lb_batch_sync(_vp(self.b))
+
+    def launches(self):
+        return int(_lib.lb_batch_launches(_vp(self.b)))
+
+    def set_tile(self, index):
+        _check(_lib.lb_batch_set_tile(_vp(self.b), int(index)), "lb_batch_set_tile")
+
+    def tile(self):
+        return int(_lib.lb_batch_get_tile(_vp(self.b)))
+
+    def tune(self, steps_per_trial=20):
+        """Pick the fastest tile shape; returns (index, trial ms per shape)."""
+        ms = np.zeros(_lib.lb_batch_tile_count())
+        _check(_lib.lb_batch_tune(_vp(self.b), int(steps_per_trial), _ptr(ms)), "lb_batch_tune")
+        return self.tile(), ms
+
+    def close(self):
+        if self.b:
+            _lib.lb_batch_destroy(_vp(self.b))
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 LB_STATIC_MAX_NODES = 1 << 20

@@ -470,6 +470,7 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
     }
     c->stencil_set = true;
     c->fast3d_ok = fused3d_applicable(c, c->fused_W, &c->fused_ng);
+    c->fast2d_ok = fused2d_applicable(c, c->fused2d_W);
     if (c->graph_valid) {
         cudaGraphExecDestroy(c->graph);
         c->graph_valid = false;
@@ -619,7 +620,9 @@ lb_status lb_set_option(lb_ctx *c, int option, long long value) {
 }
 
 int lb_fused_active(const lb_ctx *c) {
-    if (!(c && c->stencil_set && c->fast3d_ok && c->fused_enabled)) return 0;
+    if (!(c && c->stencil_set && c->fused_enabled)) return 0;
+    if (c->Q == 9) return c->fast2d_ok ? 3 : 0;
+    if (!c->fast3d_ok) return 0;
     return c->tma_ok && c->fused_tma ? 2 : 1;
 }
 

@@ -30,6 +30,7 @@ cudaError_t f32_init(lb_ctx *c, const double *rho, const double *u) {
 cudaError_t f32_step(lb_ctx *c) {
     if (c->Q == 19 && c->fast3d_ok && c->fused_enabled)
         return f32_fused3d_step(c, c->fused_W, c->fused_ng);
+    if (c->Q == 9 && c->fast2d_ok && c->fused_enabled) return f32_fused2d_step(c);
     auto k = consts_as<float>(c->k);
     const float *A = (const float *)c->f[c->cur];
     float *B = (float *)c->f[1 - c->cur];

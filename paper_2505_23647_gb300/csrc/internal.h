@@ -73,6 +73,8 @@ struct lb_ctx {
     float fused_W[7];         // group weights for the fused kernel
     int fused_ng;             // number of E8 groups the fused kernel visits
     int fused_zchunk;         // z planes per CTA (option LB_OPT_ZCHUNK)
+    bool fast2d_ok;           // the fused FP32 D2Q9 path applies (batch2d.cu)
+    float fused2d_W[5];       // its group weights: (1,0), (1,1), (2,0), (2,1), (2,2)
     bool padded;              // populations carry periodic ghost columns/rows
     bool tma_ok;              // tensor maps built for the padded buffers
     bool fused_tma;           // option LB_OPT_TMA (default on)
@@ -126,6 +128,9 @@ bool fused3d_applicable(const lb_ctx *c, float *W, int *ng);
 cudaError_t f32_fused3d_step(lb_ctx *c, const float *W, int ng);
 cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng);
 bool tma_make_maps(lb_ctx *c);
+// fused single-pass D2Q9 step (batch2d.cu)
+bool fused2d_applicable(const lb_ctx *c, float *W5);
+cudaError_t f32_fused2d_step(lb_ctx *c);
 cudaError_t ghosts_refresh(lb_ctx *c);   // padded layouts: refresh ghost cells of f[cur]
 // precision-independent (fp64.cu): reductions, pressure tensor, exp diagnostic
 cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
