@@ -194,7 +194,13 @@ __device__ __forceinline__ void tile_step(const Inst &I, int x0, int y0, int par
 #pragma unroll
         for (int i = 0; i < 9; ++i) B[(long long)i * N + s] = out[i];
     }
-    if (bad) atomicMin(&I.flags->err_step, I.flags->step);
+    // n <= 0 or NaN: one report per warp, none once the step is recorded (an
+    // unstable lattice must not turn every node into an atomic)
+    const unsigned m = __ballot_sync(0xffffffffu, bad);
+    if (m && (t & 31) == __ffs(m) - 1) {
+        const unsigned long long step = I.flags->step;
+        if (I.flags->err_step > step) atomicMin(&I.flags->err_step, step);
+    }
     __syncthreads();   // the next tile reuses ps
 }
 
