@@ -71,7 +71,12 @@ typedef enum lb_status {
 enum { LB_D2Q9 = 0, LB_D3Q19 = 1 };
 enum { LB_FP64 = 0, LB_FP32_SHIFTED = 1 };
 enum { LB_G_LITERAL = 0, LB_G_TIMES_CS2 = 1 };
-enum { LB_PSI_EXP = 0 };
+/* Pseudopotential: LB_PSI_EXP psi = exp(-1/n) (Sec. IV B); LB_PSI_EPS
+ * psi_eps = (n/(eps+n))^(1/eps) (eq. psieps, Sec. IV B / V C, e.g.
+ * eps = 14/29 with e4 = 4/5), evaluated in binary64 as
+ * RN(RN(n/RN(eps+n))^RN(1/eps)) with a correctly rounded power.  The fused
+ * kernels and batches serve LB_PSI_EXP; LB_PSI_EPS runs the two-kernel path. */
+enum { LB_PSI_EXP = 0, LB_PSI_EPS = 1 };
 
 /* Largest number of (e,-e) pairs and largest |component| of a stencil vector. */
 #define LB_MAX_PAIRS 160
@@ -84,8 +89,8 @@ typedef struct lb_params {
     double tau;         /* BGK relaxation time, > 1/2 */
     double G;           /* coupling constant (G < 0 separates phases) */
     int g_convention;   /* LB_G_LITERAL or LB_G_TIMES_CS2 */
-    int psi_kind;       /* LB_PSI_EXP: psi = exp(-1/n) */
-    double psi_eps;     /* reserved, 0 */
+    int psi_kind;       /* LB_PSI_EXP (default) or LB_PSI_EPS */
+    double psi_eps;     /* eps of LB_PSI_EPS (> 0); ignored for LB_PSI_EXP */
     double rho0_shift;  /* rho0 of the FP32 shift g_i = f_i - w_i rho0 (default 0.5) */
 } lb_params;
 
@@ -203,6 +208,12 @@ lb_status lb_set_state(lb_ctx *ctx, const double *f);
  * whose rounding could not be certified. */
 lb_status lb_exp_cr(const double *x, double *y, long long n,
                     long long *n_ambiguous);
+
+/* Diagnostic: psi[k] = psi(n_in[k]) for k < n in binary64, by the step's own
+ * device code (psi_kind as in lb_params; n_in[k] > 0).  Host arrays.
+ * Synchronous.  *n_ambiguous (may be NULL): roundings not certified. */
+lb_status lb_psi_eval(int psi_kind, double psi_eps, const double *n_in, double *psi,
+                      long long n, long long *n_ambiguous);
 
 /* Number of kernels this context has launched (for launch accounting). */
 long long lb_kernel_launches(const lb_ctx *ctx);

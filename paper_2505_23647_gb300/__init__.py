@@ -32,7 +32,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EUNSTABLE, LB_EUNSUPPORTED, LB_ESTATE 
 LB_D2Q9, LB_D3Q19 = 0, 1
 LB_FP64, LB_FP32_SHIFTED = 0, 1
 LB_G_LITERAL, LB_G_TIMES_CS2 = 0, 1
-LB_PSI_EXP = 0
+LB_PSI_EXP, LB_PSI_EPS = 0, 1
 LB_MAX_PAIRS = 160
 
 
@@ -79,6 +79,8 @@ _SIGS = {
     "lb_get_state": ([_vp, _dp], ctypes.c_int),
     "lb_set_state": ([_vp, _dp], ctypes.c_int),
     "lb_exp_cr": ([_dp, _dp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "lb_psi_eval": ([ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_longlong,
+                     ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "lb_kernel_launches": ([_vp], ctypes.c_longlong),
     "lb_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "lb_set_option": ([_vp, ctypes.c_int, ctypes.c_longlong], ctypes.c_int),
@@ -144,8 +146,9 @@ def lb_params_default():
 
 
 def make_params(lattice="D2Q9", shape=(64, 64), precision="fp64", tau=1.0, G=-5.0,
-                convention="literal", rho0_shift=0.5):
-    """lb_params from Python values; shape is (nx, ny) or (nx, ny, nz)."""
+                convention="literal", rho0_shift=0.5, psi_eps=None):
+    """lb_params from Python values; shape is (nx, ny) or (nx, ny, nz);
+    psi_eps (a float) selects psi_eps = (n/(eps+n))^(1/eps), None exp(-1/n)."""
     p = lb_params_default()
     p.lattice = {"D2Q9": LB_D2Q9, "D3Q19": LB_D3Q19}[lattice]
     p.nx, p.ny = int(shape[0]), int(shape[1])
@@ -154,6 +157,8 @@ def make_params(lattice="D2Q9", shape=(64, 64), precision="fp64", tau=1.0, G=-5.
     p.tau, p.G = float(tau), float(G)
     p.g_convention = {"literal": LB_G_LITERAL, "paper": LB_G_TIMES_CS2}[convention]
     p.rho0_shift = float(rho0_shift)
+    if psi_eps is not None:
+        p.psi_kind, p.psi_eps = LB_PSI_EPS, float(psi_eps)
     return p
 
 
@@ -258,6 +263,17 @@ def lb_exp_cr(x):
     y = np.empty_like(x)
     amb = ctypes.c_longlong(0)
     _check(_lib.lb_exp_cr(_ptr(x), _ptr(y), len(x), ctypes.byref(amb)), "lb_exp_cr")
+    return y, amb.value
+
+
+def lb_psi_eval(n, eps=None):
+    """Binary64 psi of the step's device code: exp(-1/n), or psi_eps when eps
+    is given.  Returns (psi, number of uncertified roundings)."""
+    x = _f64(n).ravel()
+    y = np.empty_like(x)
+    amb = ctypes.c_longlong(0)
+    kind, e = (LB_PSI_EXP, 0.0) if eps is None else (LB_PSI_EPS, float(eps))
+    _check(_lib.lb_psi_eval(kind, e, _ptr(x), _ptr(y), len(x), ctypes.byref(amb)), "lb_psi_eval")
     return y, amb.value
 
 
@@ -373,8 +389,9 @@ class Lattice:
 
     def __init__(self, lattice, shape_xyz, rho, stencil_bases=None, stencil_weights=None,
                  precision="fp64", tau=1.0, G=-5.0, convention="literal", rho0_shift=0.5,
-                 u=None, stream=None):
-        self.params = make_params(lattice, shape_xyz, precision, tau, G, convention, rho0_shift)
+                 u=None, stream=None, psi_eps=None):
+        self.params = make_params(lattice, shape_xyz, precision, tau, G, convention, rho0_shift,
+                                  psi_eps)
         self.D = 2 if lattice == "D2Q9" else 3
         self.Q = 9 if lattice == "D2Q9" else 19
         p = self.params

@@ -195,6 +195,9 @@ void set_consts(lb_ctx *c) {
     c->Gp = c->p.g_convention == LB_G_TIMES_CS2 ? c->p.G / 3.0 : c->p.G;
     c->k.mGp = -c->Gp;
     c->k.rho0 = c->p.rho0_shift;
+    c->k.psi_kind = c->p.psi_kind;
+    c->k.psi_eps = c->p.psi_kind == LB_PSI_EPS ? c->p.psi_eps : 0.0;
+    c->k.psi_inv = c->p.psi_kind == LB_PSI_EPS ? 1.0 / c->p.psi_eps : 0.0;
 }
 
 size_t tsize(const lb_ctx *c) { return c->p.precision == LB_FP64 ? 8 : 4; }
@@ -353,7 +356,9 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     if (p->precision != LB_FP64 && p->precision != LB_FP32_SHIFTED) return LB_EINVAL;
     if (!(p->tau > 0.5) || !std::isfinite(p->tau) || !std::isfinite(p->G)) return LB_EINVAL;
     if (p->g_convention != LB_G_LITERAL && p->g_convention != LB_G_TIMES_CS2) return LB_EINVAL;
-    if (p->psi_kind != LB_PSI_EXP) return LB_EUNSUPPORTED;
+    if (p->psi_kind != LB_PSI_EXP && p->psi_kind != LB_PSI_EPS) return LB_EINVAL;
+    if (p->psi_kind == LB_PSI_EPS && !(p->psi_eps > 0.0 && std::isfinite(p->psi_eps)))
+        return LB_EINVAL;
     if (!std::isfinite(p->rho0_shift)) return LB_EINVAL;
     const long long N = (long long)p->nx * p->ny * p->nz;
     for (long long s = 0; s < N; ++s)
@@ -596,6 +601,30 @@ lb_status lb_exp_cr(const double *x, double *y, long long n, long long *n_ambigu
     if (e == cudaSuccess) e = cudaMemcpy(&h, amb, sizeof h, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "lb_exp_cr");
+    if (n_ambiguous) *n_ambiguous = (long long)h;
+    return LB_OK;
+}
+
+lb_status lb_psi_eval(int psi_kind, double psi_eps, const double *n_in, double *psi, long long n,
+                      long long *n_ambiguous) {
+    if (psi_kind != LB_PSI_EXP && psi_kind != LB_PSI_EPS) return LB_EINVAL;
+    if (psi_kind == LB_PSI_EPS && !(psi_eps > 0.0 && std::isfinite(psi_eps))) return LB_EINVAL;
+    if (n < 0 || (n > 0 && (!n_in || !psi))) return LB_EINVAL;
+    if (n_ambiguous) *n_ambiguous = 0;
+    for (long long k = 0; k < n; ++k)
+        if (!(n_in[k] > 0.0) || !std::isfinite(n_in[k])) return LB_EINVAL;
+    if (n == 0) return LB_OK;
+    double *d = nullptr;
+    CK(cudaMalloc(&d, 2 * n * sizeof(double) + 16));
+    unsigned long long *amb = (unsigned long long *)(d + 2 * n);
+    cudaError_t e = cudaMemcpy(d, n_in, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(amb, 0, sizeof *amb);
+    if (e == cudaSuccess) e = psi_batch(d, d + n, n, psi_kind, psi_eps, amb, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(psi, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, amb, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_psi_eval");
     if (n_ambiguous) *n_ambiguous = (long long)h;
     return LB_OK;
 }

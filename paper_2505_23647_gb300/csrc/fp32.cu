@@ -38,7 +38,7 @@ cudaError_t f32_step(lb_ctx *c) {
     int gb = grid_for(c->g.N);
     if (c->Q == 9) {
         tm_begin(c, LB_KERNEL_PSI);
-        k_psi<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags);
+        k_psi<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
         k_collide<float, PairsF32, 2, 9, true>
@@ -46,7 +46,7 @@ cudaError_t f32_step(lb_ctx *c) {
         tm_end(c);
     } else {
         tm_begin(c, LB_KERNEL_PSI);
-        k_psi<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags);
+        k_psi<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
         k_collide<float, PairsF32, 3, 19, true>
@@ -63,9 +63,9 @@ cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi) {
     int gb = grid_for(c->g.N);
     const float *A = (const float *)c->f[c->cur];
     if (c->Q == 9)
-        k_density_psi64<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, c->k.rho0, n, psi, c->flags);
+        k_density_psi64<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, c->k.rho0, n, psi, c->flags, psik(c));
     else
-        k_density_psi64<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, c->k.rho0, n, psi, c->flags);
+        k_density_psi64<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, c->k.rho0, n, psi, c->flags, psik(c));
     c->launches++;
     return cudaGetLastError();
 }

@@ -31,7 +31,7 @@ cudaError_t f64_step(lb_ctx *c) {
     int gb = grid_for(c->g.N);
     if (c->Q == 9) {
         tm_begin(c, LB_KERNEL_PSI);
-        k_psi<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, psi, c->g, 0.0, c->flags);
+        k_psi<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, psi, c->g, 0.0, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
         k_collide<double, PairsF64, 2, 9, false>
@@ -39,7 +39,7 @@ cudaError_t f64_step(lb_ctx *c) {
         tm_end(c);
     } else {
         tm_begin(c, LB_KERNEL_PSI);
-        k_psi<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, psi, c->g, 0.0, c->flags);
+        k_psi<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, psi, c->g, 0.0, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
         k_collide<double, PairsF64, 3, 19, false>
@@ -55,9 +55,9 @@ cudaError_t f64_density_psi(lb_ctx *c, double *n, double *psi) {
     int gb = grid_for(c->g.N);
     const double *A = (const double *)c->f[c->cur];
     if (c->Q == 9)
-        k_density_psi64<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, c->g, 0.0, n, psi, c->flags);
+        k_density_psi64<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, c->g, 0.0, n, psi, c->flags, psik(c));
     else
-        k_density_psi64<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, c->g, 0.0, n, psi, c->flags);
+        k_density_psi64<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, c->g, 0.0, n, psi, c->flags, psik(c));
     c->launches++;
     return cudaGetLastError();
 }
@@ -350,6 +350,20 @@ __global__ void k_exp_batch(const double *__restrict__ x, double *__restrict__ y
 cudaError_t exp_batch(const double *x, double *y, long long n, unsigned long long *amb,
                       cudaStream_t s) {
     k_exp_batch<<<grid_for(n), 256, 0, s>>>(x, y, n, amb);
+    return cudaGetLastError();
+}
+
+__global__ void k_psi_batch(const double *__restrict__ n_in, double *__restrict__ psi,
+                            long long n, PsiK pk, unsigned long long *amb) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        psi[i] = psi_eval<double>(n_in[i], pk, amb);
+}
+
+cudaError_t psi_batch(const double *n_in, double *psi, long long n, int kind, double eps,
+                      unsigned long long *amb, cudaStream_t s) {
+    const PsiK pk{kind, kind == LB_PSI_EPS ? eps : 0.0, kind == LB_PSI_EPS ? 1.0 / eps : 0.0};
+    k_psi_batch<<<grid_for(n), 256, 0, s>>>(n_in, psi, n, pk, amb);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ struct Consts {
     double omega;
     double mGp;     // -G'
     double rho0;    // FP32 shift
+    int psi_kind;   // LB_PSI_EXP or LB_PSI_EPS
+    double psi_eps, psi_inv;   // eps and RN(1/eps) of psi_eps
 };
 
 struct Geom {
@@ -137,5 +139,7 @@ cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double
                        double *out_host9);
 cudaError_t ptensor(lb_ctx *c, const double *n, const double *psi, double *out);
 cudaError_t exp_batch(const double *x, double *y, long long n,
+                      unsigned long long *amb, cudaStream_t s);
+cudaError_t psi_batch(const double *n_in, double *psi, long long n, int kind, double eps,
                       unsigned long long *amb, cudaStream_t s);
 }  // namespace sclbm

@@ -66,6 +66,27 @@ struct ConstsT {
     T w[19], cw[19], omega, mGp, rho0;
 };
 
+// pseudopotential of a context: kind 0 psi = exp(-1/n); kind 1 psi_eps =
+// (n/(eps+n))^(1/eps) (eq. psieps) with inv = RN(1/eps) formed on the host
+struct PsiK {
+    int kind;
+    double eps, inv;
+};
+
+template <typename T>
+__device__ __forceinline__ T psi_eval(T n, const PsiK &pk, unsigned long long *amb);
+template <>
+__device__ __forceinline__ double psi_eval<double>(double n, const PsiK &pk,
+                                                   unsigned long long *amb) {
+    if (pk.kind == 0) return exp_cr(-1.0 / n, amb);
+    return pow_cr(__ddiv_rn(n, __dadd_rn(pk.eps, n)), pk.inv, amb);
+}
+template <>
+__device__ __forceinline__ float psi_eval<float>(float n, const PsiK &pk, unsigned long long *) {
+    if (pk.kind == 0) return expf(-1.0f / n);
+    return powf(n / ((float)pk.eps + n), (float)pk.inv);
+}
+
 template <typename T>
 __device__ __forceinline__ T psi_of(T n, unsigned long long *amb);
 template <>
@@ -118,7 +139,7 @@ __device__ __forceinline__ T sum_q(const T *fi) {
 // ---------------------------------------------------------------------------
 template <typename T, int D, int Q, bool SHIFT>
 __global__ void k_psi(const T *__restrict__ A, T *__restrict__ psi, Geom g, T rho0,
-                      Flags *flags) {
+                      Flags *flags, PsiK pk) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
         int x, y, z;
@@ -128,7 +149,7 @@ __global__ void k_psi(const T *__restrict__ A, T *__restrict__ psi, Geom g, T rh
         T n = sum_q<T, Q>(fi);
         if (SHIFT) n = n + rho0;
         if (!(n > T(0))) atomicMin(&flags->err_step, flags->step);
-        psi[s] = psi_of<T>(n, &flags->exp_amb);
+        psi[s] = psi_eval<T>(n, pk, &flags->exp_amb);
     }
 }
 
@@ -232,7 +253,7 @@ __global__ void __launch_bounds__(256) k_collide(const T *__restrict__ A, T *__r
 template <typename T, int D, int Q, bool SHIFT>
 __global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,
                                 double *__restrict__ n_out, double *__restrict__ psi_out,
-                                Flags *flags) {
+                                Flags *flags, PsiK pk) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
         int x, y, z;
@@ -245,7 +266,7 @@ __global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,
         double n = sum_q<double, Q>(fi);
         if (SHIFT) n = n + rho0;
         n_out[s] = n;
-        psi_out[s] = exp_cr(-1.0 / n, &flags->exp_amb);
+        psi_out[s] = psi_eval<double>(n, pk, &flags->exp_amb);
     }
 }
 
@@ -366,6 +387,8 @@ inline int grid_for(long long N, int block = 256, int cap = 152 * 32) {
     long long b = (N + block - 1) / block;
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
+
+inline PsiK psik(const lb_ctx *c) { return PsiK{c->k.psi_kind, c->k.psi_eps, c->k.psi_inv}; }
 
 template <typename T>
 inline ConstsT<T> consts_as(const Consts &c) {

@@ -200,6 +200,30 @@ def test_flat_interface_equilibrium(dT):
         assert 0.7 < r["delta"] / dsc < 1.0
 
 
+def test_flat_interface_psi_eps_follows_sc_maxwell():
+    """eq. psieps with the eps of the stencil (eq. eps_moments: E8 2D has
+    e4 = 4/7, eps = 10/31): a flat interface settles at the coexistence
+    densities of eq. SCMaxwell with that eps."""
+    eps = 10.0 / 31.0
+    f, df = A.psi_eps_fn(eps)
+    Gc, _ = A.critical_coupling(psi=f, dpsi=df)
+    Gp = Gc * 1.1
+    ng, nl, p0 = A.coexistence(Gp, eps, psi=f, dpsi=df, guess=(0.5, 2.0))
+    nx = 128
+    o = oracle.Oracle("D2Q9", (1, 1, nx), L.E8_2D.groups, tau=1.0, G=Gp, convention="literal",
+                      psi_kind=1, psi_eps=eps)
+    o.init_equilibrium(L.tanh_slab(nx, 1, 1, nx // 4, 3 * nx // 4, ng, nl, 3.0))
+    o.step(30000)
+    n = o.fields()["n"]
+    # second-order theory: agreement to 1.2e-4 at 10 % below G_c
+    assert abs(n.min() - ng) < 3e-4 * ng and abs(n.max() - nl) < 3e-4 * nl, (n.min(), ng, n.max(), nl)
+    # eq. SCMaxwell with eps = 0 in the measure misses the gas density by
+    # ~1e-2: the lattice follows the stencil's eps
+    ng0, nl0, _ = A.coexistence(Gp, 0.0, psi=f, dpsi=df, guess=(0.5, 2.0))
+    assert abs(n.min() - ng0) > 20 * abs(n.min() - ng)
+    assert abs(n.max() - nl0) > 20 * abs(n.max() - nl)
+
+
 def test_flat_3d_pn_constant():
     Gpaper = -E_CONST ** 2 * 1.15
     o = oracle.Oracle("D3Q19", (1, 1, 48), L.E8_3D.groups, tau=1.0, G=Gpaper,
