@@ -92,6 +92,9 @@ typedef struct lb_params {
     int psi_kind;       /* LB_PSI_EXP (default) or LB_PSI_EPS */
     double psi_eps;     /* eps of LB_PSI_EPS (> 0); ignored for LB_PSI_EXP */
     double rho0_shift;  /* rho0 of the FP32 shift g_i = f_i - w_i rho0 (default 0.5) */
+    double forcing_A;   /* F^2 forcing variant: the tensor of eq. GuoForcing is
+                           T = 2 u F - (A/tau) F F (Sec. VI); 0 (default) is
+                           Guo's T = 2 u F.  Nonzero A runs the two-kernel path. */
 } lb_params;
 
 typedef struct lb_stencil_info {

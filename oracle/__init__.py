@@ -71,11 +71,11 @@ def _load():
     lib.or_psi.restype = d
     lib.or_exp_cr.argtypes = [d]
     lib.or_exp_cr.restype = d
-    lib.or_step.argtypes = [i, i, i, i, i, dp, i, ip, dp, d, d, i, d, i]
+    lib.or_step.argtypes = [i, i, i, i, i, dp, i, ip, dp, d, d, i, d, i, d]
     lib.or_step.restype = i
     lib.or_fields.argtypes = [i, i, i, i, i, dp, i, ip, dp, d, i, d, dp, dp, dp, dp, dp]
     lib.or_fields.restype = i
-    lib.or_node_post.argtypes = [i, i, i, i, i, dp, l, l, l, i, ip, dp, d, d, i, d, dp]
+    lib.or_node_post.argtypes = [i, i, i, i, i, dp, l, l, l, i, ip, dp, d, d, i, d, dp, d]
     lib.or_node_post.restype = i
     lib.or_init_feq.argtypes = [i, i, i, i, i, dp, dp, dp]
     lib.or_init_feq.restype = i
@@ -123,7 +123,7 @@ class Oracle:
     """
 
     def __init__(self, lattice, shape, groups, tau=1.0, G=-5.0,
-                 convention="literal", psi_kind=0, psi_eps=0.0):
+                 convention="literal", psi_kind=0, psi_eps=0.0, forcing_A=0.0):
         self.D, self.Q = LATTICES[lattice]
         nz, ny, nx = shape if len(shape) == 3 else (1,) + tuple(shape)
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
@@ -133,6 +133,7 @@ class Oracle:
         self.Gp = g_prime(G, convention)
         self.psi_kind = int(psi_kind)
         self.psi_eps = float(psi_eps)
+        self.forcing_A = float(forcing_A)
         self.f = None
         self.steps_done = 0
 
@@ -166,7 +167,7 @@ class Oracle:
         lib = _load()
         rc = lib.or_step(self.D, self.Q, self.nx, self.ny, self.nz, _dp(self.f),
                          len(self.w), _ip(self.vec), _dp(self.w), self.tau, self.Gp,
-                         self.psi_kind, self.psi_eps, int(nsteps))
+                         self.psi_kind, self.psi_eps, int(nsteps), self.forcing_A)
         if rc < 0:
             raise RuntimeError(f"or_step failed ({rc})")
         self.steps_done += nsteps
@@ -195,7 +196,7 @@ class Oracle:
         rc = lib.or_node_post(self.D, self.Q, self.nx, self.ny, self.nz, _dp(self.f),
                               int(x), int(y), int(z), len(self.w), _ip(self.vec),
                               _dp(self.w), self.tau, self.Gp, self.psi_kind,
-                              self.psi_eps, _dp(out))
+                              self.psi_eps, _dp(out), self.forcing_A)
         if rc:
             raise RuntimeError(f"or_node_post failed ({rc})")
         return out

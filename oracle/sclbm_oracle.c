@@ -19,6 +19,8 @@
  *   4. j = sum_i f_i xi_i;  u = (j + F/2)/n            (Sec. II, shifted u)
  *   5. f_eq from the 2nd-order Hermite expansion       (eq. f_eq)
  *   6. S_i Guo forcing, T = 2 u F                      (eq. GuoForcing)
+ *      or, with the F^2 variant, T = 2 u F - (A/tau) F F    (Sec. VI, Appendix
+ *      on eps and e4: the tensor of eq. GuoForcing with an F F term)
  *   7. f*_i = f_i - (f_i - f_eq_i)/tau + S_i           (eqs. lbm, omega_i)
  *   8. f_i(x + xi_i) <- f*_i(x)                        (eq. lbm, streaming)
  * G' = G (literal convention, force without c_s^2) or G/3 (the paper's
@@ -128,8 +130,12 @@ static void force_at(const grid_t *g, const double *psi, long x, long y, long z,
 
 /* Collision of one node: populations fi[Q] (post-streaming), density nn,
  * force F -> post-collision fo[Q].  Also returns j + F/2 and u if asked. */
+/* kA = A/tau of the F^2 variant (0: Guo's T = 2 u F).  The source is
+ * S_i = cw_i [xi.F/cs2 + (xi xi - cs2 1):T/(2 cs2^2)] with cs2 = 1/3:
+ *   T = 2uF:        cw_i ((3 cF + 9 cu cF) - 3 u.F)
+ *   - (A/tau) F F:  - cw_i kA (4.5 cF^2 - 1.5 F.F)                         */
 static void collide_node(const grid_t *g, const double *fi, double nn,
-                         const double F[3], double omega, const double *cw,
+                         const double F[3], double omega, const double *cw, double kA,
                          double *fo, double *mom, double *uout) {
     double j[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < g->Q; i++)
@@ -144,9 +150,11 @@ static void collide_node(const grid_t *g, const double *fi, double nn,
     }
     double uu = u[0] * u[0];
     double uF = u[0] * F[0];
+    double FF = F[0] * F[0];
     for (int mu = 1; mu < g->D; mu++) {
         uu = uu + u[mu] * u[mu];
         uF = uF + u[mu] * F[mu];
+        FF = FF + F[mu] * F[mu];
     }
     for (int i = 0; i < g->Q; i++) {
         double cu = (double)g->c[i][0] * u[0];
@@ -156,7 +164,9 @@ static void collide_node(const grid_t *g, const double *fi, double nn,
             cF = cF + (double)g->c[i][mu] * F[mu];
         }
         double feq = (g->w[i] * nn) * (((1.0 + 3.0 * cu) + 4.5 * (cu * cu)) - 1.5 * uu);
-        double S = cw[i] * ((3.0 * cF + 9.0 * (cu * cF)) - 3.0 * uF);
+        double S = kA != 0.0
+            ? cw[i] * (((3.0 * cF + 9.0 * (cu * cF)) - 3.0 * uF) - kA * (4.5 * (cF * cF) - 1.5 * FF))
+            : cw[i] * ((3.0 * cF + 9.0 * (cu * cF)) - 3.0 * uF);
         fo[i] = (fi[i] - omega * (fi[i] - feq)) + S;
     }
 }
@@ -172,7 +182,7 @@ static void constants(const grid_t *g, double tau, double *omega, double *cw) {
  * 1 + (first step) at which a node had n <= 0 or NaN (the step still runs). */
 int or_step(int D, int Q, int nx, int ny, int nz, double *f, int npairs,
             const int *vec, const double *w, double tau, double Gp,
-            int psi_kind, double psi_eps, int nsteps) {
+            int psi_kind, double psi_eps, int nsteps, double forcing_A) {
     grid_t g;
     if (make_grid(&g, D, Q, nx, ny, nz)) return -1;
     double *n = malloc(sizeof(double) * g.N);
@@ -181,6 +191,7 @@ int or_step(int D, int Q, int nx, int ny, int nz, double *f, int npairs,
     if (!n || !psi || !fn) { free(n); free(psi); free(fn); return -2; }
     double omega, cw[19];
     constants(&g, tau, &omega, cw);
+    const double kA = forcing_A / tau;
     double mGp = -Gp;
     int bad = 0;
     for (int t = 0; t < nsteps; t++) {
@@ -196,7 +207,7 @@ int or_step(int D, int Q, int nx, int ny, int nz, double *f, int npairs,
                     double F[3], fi[19], fo[19];
                     force_at(&g, psi, x, y, z, npairs, vec, w, mGp, F);
                     for (int i = 0; i < g.Q; i++) fi[i] = f[(long)i * g.N + s];
-                    collide_node(&g, fi, n[s], F, omega, cw, fo, NULL, NULL);
+                    collide_node(&g, fi, n[s], F, omega, cw, kA, fo, NULL, NULL);
                     for (int i = 0; i < g.Q; i++) {
                         long d = site(&g, x + g.c[i][0], y + g.c[i][1], z + g.c[i][2]);
                         fn[(long)i * g.N + d] = fo[i];
@@ -226,7 +237,7 @@ int or_fields(int D, int Q, int nx, int ny, int nz, const double *f, int npairs,
                 double Fs[3], fi[19], fo[19], m[3], us[3];
                 force_at(&g, psi, x, y, z, npairs, vec, w, -Gp, Fs);
                 for (int i = 0; i < g.Q; i++) fi[i] = f[(long)i * g.N + s];
-                collide_node(&g, fi, n[s], Fs, omega, cw, fo, m, us);
+                collide_node(&g, fi, n[s], Fs, omega, cw, 0.0, fo, m, us);
                 for (int mu = 0; mu < D; mu++) {
                     F[(long)mu * g.N + s] = Fs[mu];
                     mom[(long)mu * g.N + s] = m[mu];
@@ -242,7 +253,7 @@ int or_fields(int D, int Q, int nx, int ny, int nz, const double *f, int npairs,
 int or_node_post(int D, int Q, int nx, int ny, int nz, const double *f, long x,
                  long y, long z, int npairs, const int *vec, const double *w,
                  double tau, double Gp, int psi_kind, double psi_eps,
-                 double *out) {
+                 double *out, double forcing_A) {
     grid_t g;
     if (make_grid(&g, D, Q, nx, ny, nz)) return -1;
     double omega, cw[19];
@@ -268,7 +279,7 @@ int or_node_post(int D, int Q, int nx, int ny, int nz, const double *f, long x,
     double pre = (-Gp) * or_psi(nn, psi_kind, psi_eps);
     double F[3] = {0.0, 0.0, 0.0};
     for (int mu = 0; mu < D; mu++) F[mu] = pre * acc[mu];
-    collide_node(&g, fi, nn, F, omega, cw, out, NULL, NULL);
+    collide_node(&g, fi, nn, F, omega, cw, forcing_A / tau, out, NULL, NULL);
     return 0;
 }
 

@@ -41,7 +41,7 @@ class lb_params(ctypes.Structure):
                 ("nz", ctypes.c_int), ("precision", ctypes.c_int), ("tau", ctypes.c_double),
                 ("G", ctypes.c_double), ("g_convention", ctypes.c_int),
                 ("psi_kind", ctypes.c_int), ("psi_eps", ctypes.c_double),
-                ("rho0_shift", ctypes.c_double)]
+                ("rho0_shift", ctypes.c_double), ("forcing_A", ctypes.c_double)]
 
 
 class lb_stencil_info(ctypes.Structure):
@@ -146,7 +146,7 @@ def lb_params_default():
 
 
 def make_params(lattice="D2Q9", shape=(64, 64), precision="fp64", tau=1.0, G=-5.0,
-                convention="literal", rho0_shift=0.5, psi_eps=None):
+                convention="literal", rho0_shift=0.5, psi_eps=None, forcing_A=0.0):
     """lb_params from Python values; shape is (nx, ny) or (nx, ny, nz);
     psi_eps (a float) selects psi_eps = (n/(eps+n))^(1/eps), None exp(-1/n)."""
     p = lb_params_default()
@@ -159,6 +159,7 @@ def make_params(lattice="D2Q9", shape=(64, 64), precision="fp64", tau=1.0, G=-5.
     p.rho0_shift = float(rho0_shift)
     if psi_eps is not None:
         p.psi_kind, p.psi_eps = LB_PSI_EPS, float(psi_eps)
+    p.forcing_A = float(forcing_A)
     return p
 
 
@@ -389,9 +390,9 @@ class Lattice:
 
     def __init__(self, lattice, shape_xyz, rho, stencil_bases=None, stencil_weights=None,
                  precision="fp64", tau=1.0, G=-5.0, convention="literal", rho0_shift=0.5,
-                 u=None, stream=None, psi_eps=None):
+                 u=None, stream=None, psi_eps=None, forcing_A=0.0):
         self.params = make_params(lattice, shape_xyz, precision, tau, G, convention, rho0_shift,
-                                  psi_eps)
+                                  psi_eps, forcing_A)
         self.D = 2 if lattice == "D2Q9" else 3
         self.Q = 9 if lattice == "D2Q9" else 19
         p = self.params

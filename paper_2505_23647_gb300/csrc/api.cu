@@ -195,6 +195,7 @@ void set_consts(lb_ctx *c) {
     c->Gp = c->p.g_convention == LB_G_TIMES_CS2 ? c->p.G / 3.0 : c->p.G;
     c->k.mGp = -c->Gp;
     c->k.rho0 = c->p.rho0_shift;
+    c->k.kA = c->p.forcing_A / tau;
     c->k.psi_kind = c->p.psi_kind;
     c->k.psi_eps = c->p.psi_kind == LB_PSI_EPS ? c->p.psi_eps : 0.0;
     c->k.psi_inv = c->p.psi_kind == LB_PSI_EPS ? 1.0 / c->p.psi_eps : 0.0;
@@ -326,6 +327,7 @@ lb_status lb_params_default(lb_params *p) {
     p->psi_kind = LB_PSI_EXP;
     p->psi_eps = 0.0;
     p->rho0_shift = 0.5;
+    p->forcing_A = 0.0;
     return LB_OK;
 }
 
@@ -359,7 +361,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     if (p->psi_kind != LB_PSI_EXP && p->psi_kind != LB_PSI_EPS) return LB_EINVAL;
     if (p->psi_kind == LB_PSI_EPS && !(p->psi_eps > 0.0 && std::isfinite(p->psi_eps)))
         return LB_EINVAL;
-    if (!std::isfinite(p->rho0_shift)) return LB_EINVAL;
+    if (!std::isfinite(p->rho0_shift) || !std::isfinite(p->forcing_A)) return LB_EINVAL;
     const long long N = (long long)p->nx * p->ny * p->nz;
     for (long long s = 0; s < N; ++s)
         if (!(rho_init[s] > 0.0) || !std::isfinite(rho_init[s])) return LB_EINVAL;

@@ -290,7 +290,9 @@ int resident_grid(int s) {
 // The 2D fused path applies to a shifted-binary32 D2Q9 context whose
 // stencil uses only the five 2D groups up to (2,2).
 bool fused2d_applicable(const lb_ctx *c, float *W5) {
-    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 9 || c->p.psi_kind != LB_PSI_EXP) return false;
+    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 9 || c->p.psi_kind != LB_PSI_EXP ||
+        c->p.forcing_A != 0.0)
+        return false;
     if (c->g.nx < 4 || c->g.ny < 4) return false;
     if ((long long)9 * c->g.N >= (1LL << 31)) return false;
     static const int bases[5][2] = {{1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};

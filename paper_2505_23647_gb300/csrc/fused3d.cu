@@ -171,7 +171,9 @@ constexpr int smem_bytes() {
 }  // namespace fz
 
 bool fused3d_applicable(const lb_ctx *c, float *W, int *ng) {
-    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 19 || c->p.psi_kind != LB_PSI_EXP) return false;
+    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 19 || c->p.psi_kind != LB_PSI_EXP ||
+        c->p.forcing_A != 0.0)
+        return false;
     if (c->g.nx < 8 || c->g.ny < 8 || c->g.nz < 8) return false;
     if ((long long)19 * c->g.Np >= (1LL << 31)) return false;
     static const int bases[7][3] = {{1, 0, 0}, {1, 1, 0}, {1, 1, 1}, {2, 0, 0},

@@ -35,6 +35,7 @@ struct Consts {
     double omega;
     double mGp;     // -G'
     double rho0;    // FP32 shift
+    double kA;      // A/tau of the F^2 forcing variant (0: Guo's T = 2 u F)
     int psi_kind;   // LB_PSI_EXP or LB_PSI_EPS
     double psi_eps, psi_inv;   // eps and RN(1/eps) of psi_eps
 };

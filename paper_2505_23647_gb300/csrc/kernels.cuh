@@ -63,7 +63,7 @@ __device__ __forceinline__ void coords(const Geom &g, long long s, int &x, int &
 
 template <typename T>
 struct ConstsT {
-    T w[19], cw[19], omega, mGp, rho0;
+    T w[19], cw[19], omega, mGp, rho0, kA;
 };
 
 // pseudopotential of a context: kind 0 psi = exp(-1/n); kind 1 psi_eps =
@@ -199,18 +199,24 @@ __device__ __forceinline__ void collide(const T *fi, T n, T dn, const T *F, cons
         if (momo) momo[mu] = m;
         if (uo) uo[mu] = u[mu];
     }
-    T uu = u[0] * u[0], uF = u[0] * F[0];
+    T uu = u[0] * u[0], uF = u[0] * F[0], FF = F[0] * F[0];
 #pragma unroll
     for (int mu = 1; mu < D; ++mu) {
         uu = uu + u[mu] * u[mu];
         uF = uF + u[mu] * F[mu];
+        FF = FF + F[mu] * F[mu];
     }
     if (!fo) return;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T cu = cdot<Q, D, T>(i, u);
         const T cF = cdot<Q, D, T>(i, F);
-        const T S = k.cw[i] * ((T(3) * cF + T(9) * (cu * cF)) - T(3) * uF);
+        // Guo source with T = 2uF, or with the F^2 variant T = 2uF - (A/tau) F F
+        // (kA = A/tau): the extra term - cw kA (4.5 cF^2 - 1.5 F.F)
+        const T S = k.kA != T(0)
+            ? k.cw[i] * (((T(3) * cF + T(9) * (cu * cF)) - T(3) * uF) -
+                         k.kA * (T(4.5) * (cF * cF) - T(1.5) * FF))
+            : k.cw[i] * ((T(3) * cF + T(9) * (cu * cF)) - T(3) * uF);
         if (SHIFT) {
             const T geq = k.w[i] * (dn + n * ((T(3) * cu + T(4.5) * (cu * cu)) - T(1.5) * uu));
             fo[i] = (fi[i] - k.omega * (fi[i] - geq)) + S;
@@ -400,6 +406,7 @@ inline ConstsT<T> consts_as(const Consts &c) {
     r.omega = (T)c.omega;
     r.mGp = (T)c.mGp;
     r.rho0 = (T)c.rho0;
+    r.kA = (T)c.kA;
     return r;
 }
 

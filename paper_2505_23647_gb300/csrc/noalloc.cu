@@ -163,6 +163,7 @@ extern "C" lb_status lb_step_fp64_static(int lattice, int nx, int ny, int nz, do
     const double Gp = g_convention == LB_G_TIMES_CS2 ? G / 3.0 : G;
     k.mGp = -Gp;
     k.rho0 = 0.0;
+    k.kA = 0.0;   // Guo's T = 2 u F (no F^2 term on this entry point)
     Geom g = {nx, ny, nz, N, nx, ny, 0, 0, N};
 
     double *scratch = nullptr;

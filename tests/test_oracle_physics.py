@@ -224,6 +224,60 @@ def test_flat_interface_psi_eps_follows_sc_maxwell():
     assert abs(n.max() - nl0) > 20 * abs(n.max() - nl)
 
 
+@pytest.mark.parametrize("lattice,shape,stencil", [("D2Q9", (1, 9, 11), L.E8_2D),
+                                                   ("D3Q19", (7, 8, 9), L.E4_3D)])
+def test_f2_forcing_source_moments(lattice, shape, stencil):
+    """F^2 variant (Sec. VI): with T = 2 u F - (A/tau) F F in eq. GuoForcing,
+    the source's moments are sum S = 0, sum xi S = (1 - 1/(2 tau)) F and
+    sum xi xi S = (1 - 1/(2 tau)) sym(T): the F F part leaves mass and
+    momentum alone and adds -(1 - 1/(2 tau)) (A/tau) F F to the second
+    moment.  Checked on the difference of post-collision populations with
+    and without it (everything else in the update is identical)."""
+    rng = np.random.default_rng(5)
+    tau, A, G = 0.8, 0.37, -4.0
+    C = oracle.C9 if lattice == "D2Q9" else oracle.C19
+    rho = 1.0 + 0.6 * rng.random(shape)
+    o0 = oracle.Oracle(lattice, shape, stencil.groups, tau=tau, G=G)
+    o0.init_equilibrium(rho)
+    o0.f = o0.f * (1.0 + 0.05 * rng.random(o0.f.shape))
+    oA = oracle.Oracle(lattice, shape, stencil.groups, tau=tau, G=G, forcing_A=A)
+    oA.f = o0.f.copy()
+    F = o0.fields()["F"]
+    pref = 1.0 - 1.0 / (2.0 * tau)
+    worst = 0.0
+    for _ in range(12):
+        z, y, x = (int(rng.integers(0, s)) for s in shape)
+        d = oA.node_post(x, y, z) - o0.node_post(x, y, z)
+        Fn = F[:, z, y, x]
+        D = len(Fn)
+        assert abs(d.sum()) < 1e-15
+        for a in range(D):
+            assert abs(np.dot(d, C[:, a])) < 1e-15
+            for b in range(D):
+                m2 = np.dot(d, C[:, a] * C[:, b])
+                want = -pref * (A / tau) * Fn[a] * Fn[b]
+                assert abs(m2 - want) < 1e-15 + 1e-12 * abs(want)
+                worst = max(worst, abs(want))
+    assert worst > 1e-6          # the term was exercised
+
+
+def test_f2_forcing_shifts_coexistence():
+    """The F F term adds eps_F to eps (Sec. VI), so a flat interface settles
+    at other coexistence densities than with Guo's T = 2 u F."""
+    Gp = -E_CONST ** 2 / 3.0 * 1.2
+    nx = 64
+    res = []
+    for A in (0.0, 0.5):
+        o = oracle.Oracle("D2Q9", (1, 1, nx), L.E4_2D.groups, tau=1.0, G=Gp, convention="literal",
+                          forcing_A=A)
+        o.init_equilibrium(L.tanh_slab(nx, 1, 1, nx // 4, 3 * nx // 4, 0.3, 2.2, 3.0))
+        o.step(12000)
+        n = o.fields()["n"]
+        res.append((n.min(), n.max()))
+    (g0, l0), (gA, lA) = res
+    assert abs(gA - g0) > 1e-3 * g0 and abs(lA - l0) > 1e-3 * l0
+
+
 def test_flat_3d_pn_constant():
     Gpaper = -E_CONST ** 2 * 1.15
     o = oracle.Oracle("D3Q19", (1, 1, 48), L.E8_3D.groups, tau=1.0, G=Gpaper,
