@@ -304,6 +304,46 @@ int lb_batch_get_tile(const lb_batch *batch);
  * trial times.  Synchronous; allocates a copy of every member's state. */
 lb_status lb_batch_tune(lb_batch *batch, int steps_per_trial, double *ms_out);
 
+/* ---- adjoint: gradients of the surface tension ------------------------------
+ *
+ * The discrete adjoint of lb_step in binary64 (eqs. lbm, omega_i, f_eq,
+ * GuoForcing, sc_f read backwards), for gradients of the flat-interface
+ * surface tension sigma_0 (Sec. V A; the Appendix E pressure tensor summed
+ * over the lattice is (G'/2) sum_x psi(x) sum_e W(e) psi(x+e)(e_x^2 - e_y^2))
+ * or of any loss whose gradient with respect to the state the caller
+ * supplies.  An adjoint belongs to one context (any lattice, precision and
+ * pseudopotential; LB_EUNSUPPORTED with the F^2 forcing variant); its
+ * adjoint variable lam = dL/d(state) has the layout of lb_get_state.
+ *
+ * Typical use, with checkpoints every K steps (a checkpoint is lb_get_state
+ * / lb_set_state):  step forward saving checkpoints; lb_adjoint_seed_sigma
+ * (or lb_adjoint_set) at the final state; then for each segment, last first:
+ * lb_set_state(checkpoint); lb_adjoint_run(K).  lb_adjoint_run recomputes
+ * the segment's forward steps with the context's own step (the context ends
+ * K steps later), records the states in binary64 (K [Q][N] arrays of device
+ * memory) and carries lam back to the checkpoint, adding the segment's terms
+ * to the gradients.  lb_adjoint_gradient returns dL/dW for each stencil group
+ * (the order of lb_set_stencil) and dL/dG; sums are in a fixed order, so
+ * results are reproducible. */
+typedef struct lb_adjoint lb_adjoint;
+
+lb_status lb_adjoint_create(lb_ctx *ctx, lb_adjoint **out);
+lb_status lb_adjoint_destroy(lb_adjoint *adj);
+/* lam := host array [Q][N] (NULL: zero). */
+lb_status lb_adjoint_set(lb_adjoint *adj, const double *lam);
+lb_status lb_adjoint_get(lb_adjoint *adj, double *lam);
+/* Clear the accumulated parameter gradients. */
+lb_status lb_adjoint_zero_grad(lb_adjoint *adj);
+/* sigma_0 of the context's current state (a flat slab with gradients along
+ * x and n_interfaces interfaces): writes *sigma (may be NULL), sets lam =
+ * dsigma/d(state) and adds sigma's explicit dependence on W and G to the
+ * gradients. */
+lb_status lb_adjoint_seed_sigma(lb_adjoint *adj, int n_interfaces, double *sigma);
+/* Carry lam back over the next nsteps steps of the context (see above). */
+lb_status lb_adjoint_run(lb_adjoint *adj, int nsteps);
+/* dL/dW per stencil group (n_groups doubles, may be NULL) and dL/dG. */
+lb_status lb_adjoint_gradient(lb_adjoint *adj, double *dW, double *dG);
+
 /* Largest lattice (nodes) lb_step_fp64_static accepts: 2^20, i.e. a fixed
  * 8 MiB of device memory (plus 64 bytes of counters) per GPU. */
 #define LB_STATIC_MAX_NODES (1LL << 20)

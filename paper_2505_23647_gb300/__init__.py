@@ -89,6 +89,14 @@ _SIGS = {
                              _ip, _dp, _vp, _vp, _vp], ctypes.c_int),
     "lb_fused_active": ([_vp], ctypes.c_int),
     "lb_timing_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "lb_adjoint_create": ([_vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "lb_adjoint_destroy": ([_vp], ctypes.c_int),
+    "lb_adjoint_set": ([_vp, _dp], ctypes.c_int),
+    "lb_adjoint_get": ([_vp, _dp], ctypes.c_int),
+    "lb_adjoint_zero_grad": ([_vp], ctypes.c_int),
+    "lb_adjoint_seed_sigma": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
+    "lb_adjoint_run": ([_vp, ctypes.c_int], ctypes.c_int),
+    "lb_adjoint_gradient": ([_vp, _dp, _dp], ctypes.c_int),
     "lb_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(_vp)],
                         ctypes.c_int),
     "lb_batch_destroy": ([_vp], ctypes.c_int),
@@ -405,6 +413,8 @@ class Lattice:
 
     def set_stencil(self, bases, weights):
         self.info = lb_set_stencil(self.ctx, self.D, bases, weights)
+        self.stencil_bases = np.asarray(bases)
+        self.stencil_weights = np.asarray(weights, dtype=np.float64)
         return self.info
 
     def step(self, n=1):

@@ -1,0 +1,143 @@
+"""Gradients of the flat-interface surface tension through the step
+(``lb_adjoint_*``), with checkpointed recomputation, and a
+``torch.autograd.Function`` on top.
+
+Every step, forward and backward, runs in the library's kernels; this module
+only moves checkpoints (``lb_get_state`` / ``lb_set_state``) and arguments.
+"""
+import ctypes
+
+import numpy as np
+
+from . import LbError, Lattice, _check, _lib, _ptr, _vp
+
+
+class Adjoint:
+    """The adjoint of one :class:`Lattice` (see ``lb_adjoint_*`` in sclbm.h)."""
+
+    def __init__(self, lattice):
+        self.lat = lattice
+        out = _vp()
+        _check(_lib.lb_adjoint_create(_vp(lattice.ctx), ctypes.byref(out)), "lb_adjoint_create")
+        self.a = out.value
+
+    def set(self, lam=None):
+        if lam is None:
+            _check(_lib.lb_adjoint_set(_vp(self.a), None), "lb_adjoint_set")
+        else:
+            lam = np.ascontiguousarray(lam, dtype=np.float64).reshape(-1)
+            if lam.size != self.lat.Q * self.lat.N:
+                raise ValueError("lam must have Q x N entries")
+            _check(_lib.lb_adjoint_set(_vp(self.a), _ptr(lam)), "lb_adjoint_set")
+
+    def get(self):
+        lam = np.empty(self.lat.Q * self.lat.N)
+        _check(_lib.lb_adjoint_get(_vp(self.a), _ptr(lam)), "lb_adjoint_get")
+        return lam.reshape((self.lat.Q,) + self.lat.shape)
+
+    def zero_grad(self):
+        _check(_lib.lb_adjoint_zero_grad(_vp(self.a)), "lb_adjoint_zero_grad")
+
+    def seed_sigma(self, n_interfaces=2):
+        s = ctypes.c_double(0.0)
+        _check(_lib.lb_adjoint_seed_sigma(_vp(self.a), int(n_interfaces), ctypes.byref(s)),
+               "lb_adjoint_seed_sigma")
+        return s.value
+
+    def run(self, nsteps):
+        _check(_lib.lb_adjoint_run(_vp(self.a), int(nsteps)), "lb_adjoint_run")
+
+    def gradient(self):
+        """(dL/dW per stencil group, dL/dG)."""
+        dW = np.zeros(len(self.lat.stencil_weights))
+        dG = ctypes.c_double(0.0)
+        _check(_lib.lb_adjoint_gradient(_vp(self.a), _ptr(dW), ctypes.byref(dG)),
+               "lb_adjoint_gradient")
+        return dW, dG.value
+
+    def close(self):
+        if self.a:
+            _lib.lb_adjoint_destroy(_vp(self.a))
+            self.a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sigma_and_gradient(lattice, steps, checkpoint_every=100, n_interfaces=2):
+    """sigma_0 after ``steps`` steps of ``lattice`` (a flat slab along x) and its
+    gradient with respect to the stencil group weights, G and the initial
+    state.  The forward run keeps a checkpoint every ``checkpoint_every``
+    steps; the backward pass recomputes one segment at a time.  The lattice
+    ends ``steps`` steps after its initial state.  Returns
+    (sigma, dW [groups], dG, dsigma/d(initial state))."""
+    K = max(1, int(checkpoint_every))
+    ckpts = []
+    done = 0
+    while done < steps:
+        ckpts.append((done, lattice.state()))
+        k = min(K, steps - done)
+        lattice.step(k)
+        done += k
+    adj = Adjoint(lattice)
+    try:
+        sigma = adj.seed_sigma(n_interfaces)
+        for start, st in reversed(ckpts):
+            lattice.set_state(st)
+            adj.run(min(K, steps - start))
+        dW, dG = adj.gradient()
+        lam0 = adj.get()
+    finally:
+        adj.close()
+    return sigma, dW, dG, lam0
+
+
+_FN = None
+
+
+def _torch_function():
+    global _FN
+    if _FN is not None:
+        return _FN
+    import torch
+
+    class FlatSigma(torch.autograd.Function):
+        """sigma_0(W, G) of a flat slab after a fixed number of steps from a
+        fixed initial density; backward by the adjoint (computed with the
+        forward, checkpointed)."""
+
+        @staticmethod
+        def forward(ctx, W, G, spec):
+            lat = Lattice(spec["lattice"], spec["shape"], spec["rho"], spec["bases"],
+                          W.detach().cpu().numpy().astype(np.float64), precision=spec.get("precision", "fp64"),
+                          tau=spec.get("tau", 1.0), G=float(G), convention=spec.get("convention", "literal"),
+                          psi_eps=spec.get("psi_eps"))
+            try:
+                sigma, dW, dG, _ = sigma_and_gradient(lat, spec["steps"], spec.get("checkpoint_every", 100),
+                                                      spec.get("n_interfaces", 2))
+            finally:
+                lat.close()
+            ctx.save_for_backward(torch.as_tensor(dW, dtype=W.dtype), torch.as_tensor(dG, dtype=W.dtype))
+            return W.new_tensor(sigma)
+
+        @staticmethod
+        def backward(ctx, g):
+            dW, dG = ctx.saved_tensors
+            return g * dW, g * dG, None
+
+    _FN = FlatSigma
+    return FlatSigma
+
+
+def flat_sigma(W, G, spec):
+    """Differentiable sigma_0 (torch): W a tensor of group weights (the order
+    of spec['bases']), G a scalar tensor; spec holds lattice, shape, rho,
+    bases, steps and optionally precision, tau, convention, psi_eps,
+    checkpoint_every, n_interfaces."""
+    return _torch_function().apply(W, G, spec)
+
+
+__all__ = ["Adjoint", "sigma_and_gradient", "flat_sigma", "LbError"]

@@ -28,6 +28,7 @@ UNITS = {
     "fused3d_tma.cu": [],
     "noalloc.cu": ["-fmad=false"],
     "batch2d.cu": [],
+    "adjoint.cu": [],
 }
 
 

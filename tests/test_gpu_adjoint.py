@@ -1,0 +1,161 @@
+"""The GPU adjoint (lb_adjoint_*, binary64) against the oracle's adjoint
+(oracle/adjoint.py, itself pinned to central finite differences of the
+oracle's forward step) and against finite differences of the GPU's own
+forward runs; checkpointing changes nothing; the torch.autograd.Function
+returns the same gradient; and a gradient solve of the paper's surface
+tension knob (Table tab:e4_tuning_6, sigma0_hat) hits a target sigma_0."""
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+import lbinputs as L
+import oracle
+from oracle import adjoint as OAD
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2505_23647_gb300")
+AD = pytest.importorskip("paper_2505_23647_gb300.adjoint")
+
+N_GAS, N_LIQ = 0.456, 2.25
+
+CASES = [
+    ("D2Q9", (24, 5), L.E8_2D, 1.0, -3.0, "literal", None, 12),
+    ("D3Q19", (20, 4, 3), L.E4_3D, 0.8, -4.0, "literal", None, 8),
+    ("D2Q9", (22, 4), L.E6_2D, 1.3, -9.0, "paper", None, 10),
+    ("D2Q9", (26, 4), L.E8_2D, 1.0, -2.7, "literal", 10.0 / 31.0, 10),
+]
+
+
+def _rho(shape):
+    nx, ny = shape[0], shape[1]
+    nz = shape[2] if len(shape) > 2 else 1
+    return L.tanh_slab(nx, ny, nz, nx // 4, 3 * nx // 4, N_GAS, N_LIQ, 2.0)
+
+
+def _lat(lattice, shape, st, tau, G, conv, eps, precision="fp64", weights=None):
+    return P.Lattice(lattice, shape, _rho(shape), st.bases,
+                     st.weights if weights is None else weights, precision=precision, tau=tau,
+                     G=G, convention=conv, psi_eps=eps)
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,eps,steps", CASES)
+def test_gpu_adjoint_matches_oracle_adjoint(lattice, shape, st, tau, G, conv, eps, steps):
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    g0 = lat.state()
+    sigma, dW, dG, lam0 = AD.sigma_and_gradient(lat, steps, checkpoint_every=steps)
+    lat.close()
+    nz = shape[2] if len(shape) > 2 else 1
+    o = oracle.Oracle(lattice, (nz, shape[1], shape[0]), st.groups, tau=tau, G=G, convention=conv,
+                      psi_kind=0 if eps is None else 1, psi_eps=0.0 if eps is None else eps)
+    s_o, lam_o, dW_o, dGp_o = OAD.gradient(o, g0.reshape((o.Q, nz, shape[1], shape[0])), steps, 2)
+    dG_o = dGp_o / 3.0 if conv == "paper" else dGp_o
+    assert abs(sigma - s_o) < 1e-12 * abs(s_o)
+    assert _rel(dW, dW_o) < 1e-10, (dW, dW_o)
+    assert abs(dG - dG_o) < 1e-10 * abs(dG_o)
+    assert _rel(lam0.reshape(lam_o.shape), lam_o) < 1e-10
+
+
+def test_checkpointing_changes_nothing():
+    lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
+    res = []
+    for K in (60, 7, 1):
+        lat = _lat(lattice, shape, st, tau, G, conv, eps)
+        res.append(AD.sigma_and_gradient(lat, 60, checkpoint_every=K))
+        lat.close()
+    for r in res[1:]:
+        assert r[0] == res[0][0]
+        assert np.array_equal(r[1], res[0][1]) and r[2] == res[0][2]
+        assert np.array_equal(r[3], res[0][3])
+
+
+def test_gradient_matches_finite_differences_of_gpu_runs():
+    lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
+    steps = 200
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    _, dW, dG, _ = AD.sigma_and_gradient(lat, steps, checkpoint_every=50)
+    lat.close()
+
+    def sigma_of(weights, Gv):
+        l = _lat(lattice, shape, st, tau, Gv, conv, eps, weights=weights)
+        l.step(steps)
+        a = AD.Adjoint(l)
+        s = a.seed_sigma(2)
+        a.close()
+        l.close()
+        return s
+
+    w0 = st.weights.copy()
+    for q in range(len(w0)):
+        h = 1e-6 * w0[q]
+        wp, wm = w0.copy(), w0.copy()
+        wp[q] += h
+        wm[q] -= h
+        fd = (sigma_of(wp, G) - sigma_of(wm, G)) / (2 * h)
+        assert abs(dW[q] - fd) < 1e-6 * abs(fd) + 1e-9, (q, dW[q], fd)
+    h = 1e-6 * abs(G)
+    fd = (sigma_of(w0, G + h) - sigma_of(w0, G - h)) / (2 * h)
+    assert abs(dG - fd) < 1e-6 * abs(fd)
+
+
+def test_fp32_forward_gradient_close_to_fp64():
+    lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
+    out = {}
+    for prec in ("fp64", "fp32"):
+        lat = _lat(lattice, (64, 4), st, tau, G, conv, eps, precision=prec)
+        out[prec] = AD.sigma_and_gradient(lat, 500, checkpoint_every=100)
+        lat.close()
+    s64, w64, g64, _ = out["fp64"]
+    s32, w32, g32, _ = out["fp32"]
+    assert abs(s32 - s64) < 1e-4 * abs(s64)
+    assert _rel(w32, w64) < 1e-3 and abs(g32 - g64) < 1e-3 * abs(g64)
+
+
+def test_torch_autograd_function():
+    torch = pytest.importorskip("torch")
+    lattice, shape, st, tau, G, conv, eps, steps = CASES[0]
+    spec = dict(lattice=lattice, shape=shape, rho=_rho(shape), bases=st.bases, steps=steps,
+                tau=tau, convention=conv, checkpoint_every=5)
+    W = torch.tensor(st.weights, dtype=torch.float64, requires_grad=True)
+    Gt = torch.tensor(G, dtype=torch.float64, requires_grad=True)
+    s = AD.flat_sigma(W, Gt, spec)
+    (2.0 * s).backward()
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    sigma, dW, dG, _ = AD.sigma_and_gradient(lat, steps, checkpoint_every=steps)
+    lat.close()
+    assert float(s.detach()) == sigma
+    assert np.allclose(W.grad.numpy(), 2.0 * dW, rtol=0, atol=0)
+    assert float(Gt.grad) == 2.0 * dG
+
+
+def test_gradient_solve_hits_target_sigma():
+    """Replace the hand tuning of Sec. V with a gradient solve: Newton on the
+    knob sigma0_hat of Table tab:e4_tuning_6 (weights linear in the knob)
+    until sigma_0 of a relaxed slab is 1.15 x its untuned value."""
+    nx, ny, steps, G = 64, 4, 1500, -3.0
+    rho = L.tanh_slab(nx, ny, 1, 16, 48, N_GAS, N_LIQ, 2.0)
+    # d W / d knob of the table (groups (1,0), (1,1), (2,0), (2,2))
+    slope = np.array([4 / 3, -1 / 6, -5 / 24, -1 / 48])
+
+    def run(s0):
+        st = L.stencil_e4_tuning_6(2, Fr(s0).limit_denominator(10 ** 12))
+        lat = P.Lattice("D2Q9", (nx, ny), rho, st.bases, st.weights, G=G)
+        sigma, dW, _, _ = AD.sigma_and_gradient(lat, steps, checkpoint_every=250)
+        lat.close()
+        return sigma, float(np.dot(dW, slope))
+
+    s0 = 0.0
+    sigma0, _ = run(s0)
+    target = 1.15 * sigma0
+    for _ in range(8):
+        sigma, dsig = run(s0)
+        if abs(sigma / target - 1.0) < 1e-3:
+            break
+        s0 -= (sigma - target) / dsig
+    assert abs(sigma / target - 1.0) < 1e-3, (s0, sigma, target)

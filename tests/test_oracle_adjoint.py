@@ -1,0 +1,86 @@
+"""Pin of the oracle's adjoint (oracle/adjoint.py) to the oracle's forward step:
+its numpy forward reproduces the C oracle, and the gradient of the flat-slab
+surface tension sigma_0 (Sec. V A, from the Appendix E pressure tensor summed
+over the lattice) with respect to the stencil group weights, G and the
+initial populations equals central finite differences of the C oracle run
+(h = 1e-6 relative for the parameters, 1e-4 for the populations)."""
+import numpy as np
+import pytest
+
+import lbinputs as L
+import oracle
+from oracle import adjoint as AD
+
+CASES = [
+    ("D2Q9", (1, 5, 24), L.E8_2D, 1.0, -3.0, "literal", 12),
+    ("D3Q19", (3, 4, 20), L.E4_3D, 0.8, -4.0, "literal", 8),
+    ("D2Q9", (1, 4, 22), L.E6_2D, 1.3, -9.0, "paper", 10),
+]
+
+
+def _setup(lattice, shape, st, tau, G, conv):
+    nz, ny, nx = shape
+    rho = L.tanh_slab(nx, ny, nz, nx // 4, 3 * nx // 4, 0.456, 2.25, 2.0)
+    o = oracle.Oracle(lattice, shape, st.groups, tau=tau, G=G, convention=conv)
+    o.init_equilibrium(rho)
+    return o
+
+
+def _sigma_after(lattice, shape, groups, tau, G, conv, g0, steps):
+    o = oracle.Oracle(lattice, shape, groups, tau=tau, G=G, convention=conv)
+    o.f = g0.copy()
+    o.step(steps)
+    return AD.sigma_flat(o, o.f, 2)[0]
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,steps", CASES)
+def test_numpy_forward_matches_c_oracle(lattice, shape, st, tau, G, conv, steps):
+    o = _setup(lattice, shape, st, tau, G, conv)
+    g = o.f.copy()
+    for _ in range(3):
+        g = AD.step_forward(o, g)
+    o.step(3)
+    assert np.max(np.abs(g - o.f)) < 1e-14
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,steps", CASES)
+def test_sigma_formula_matches_pressure_tensor(lattice, shape, st, tau, G, conv, steps):
+    o = _setup(lattice, shape, st, tau, G, conv)
+    o.step(steps)
+    s = AD.sigma_flat(o, o.f, 2)[0]
+    P = o.pressure_tensor()
+    PT = P[2] if o.D == 2 else P[3]
+    assert abs(s - float(np.sum(P[0] - PT)) / 2) < 1e-12 * abs(s)
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,steps", CASES)
+def test_adjoint_gradient_matches_finite_differences(lattice, shape, st, tau, G, conv, steps):
+    o = _setup(lattice, shape, st, tau, G, conv)
+    g0 = o.f.copy()
+    sigma, lam, dW, dGp = AD.gradient(o, g0, steps, 2)
+    assert abs(sigma - _sigma_after(lattice, shape, st.groups, tau, G, conv, g0, steps)) < 1e-13
+    # group weights
+    for q, (b, wq) in enumerate(st.groups):
+        h = 1e-6 * float(wq)
+        gp = [(bb, float(ww) + (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        gm = [(bb, float(ww) - (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        fd = (_sigma_after(lattice, shape, gp, tau, G, conv, g0, steps) -
+              _sigma_after(lattice, shape, gm, tau, G, conv, g0, steps)) / (2 * h)
+        assert abs(dW[q] - fd) < 1e-6 * max(abs(fd), 1e-3 * abs(sigma) / float(wq)), (q, dW[q], fd)
+    # coupling (G' = G or G/3)
+    h = 1e-6 * abs(G)
+    fd = (_sigma_after(lattice, shape, st.groups, tau, G + h, conv, g0, steps) -
+          _sigma_after(lattice, shape, st.groups, tau, G - h, conv, g0, steps)) / (2 * h)
+    dG = dGp * (1.0 / 3.0 if conv == "paper" else 1.0)
+    assert abs(dG - fd) < 1e-6 * abs(fd), (dG, fd)
+    # initial populations, a few entries
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        idx = tuple(int(rng.integers(0, s)) for s in g0.shape)
+        h = 1e-4 * abs(g0[idx])      # sigma ~ 0.2: FD rounding 1e-16 sigma / h stays below 1e-11
+        gp, gm = g0.copy(), g0.copy()
+        gp[idx] += h
+        gm[idx] -= h
+        fd = (_sigma_after(lattice, shape, st.groups, tau, G, conv, gp, steps) -
+              _sigma_after(lattice, shape, st.groups, tau, G, conv, gm, steps)) / (2 * h)
+        assert abs(lam[idx] - fd) < 1e-6 * abs(fd) + 1e-10, (idx, lam[idx], fd)
