@@ -364,6 +364,29 @@ def run_gb300(args, dist, rank, ws):
         for l in lats:
             l.close()
 
+    # adjoint: gradients of sigma_0 through the step (D2Q9 E8, 512^2 periodic
+    # box holding a flat slab, FP32 forward, binary64 adjoint, checkpoint every
+    # 100 steps): forward with checkpoints, then every segment recomputed and
+    # carried back; adjoint steps per second of the whole procedure
+    adjoint = None
+    if not args.no_adjoint:
+        import paper_2505_23647_gb300.adjoint as PA
+        na, ka, ca = 512, 400, 100
+        rho_a = L.tanh_slab(na, na, 1, na // 4, 3 * na // 4, 0.456, 2.25, 2.0)
+        lat_a = P.Lattice("D2Q9", (na, na), rho_a, L.E8_2D.bases, L.E8_2D.weights, precision="fp32",
+                          tau=1.0, G=-3.0, convention="literal", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sig, dWa, dGa, _ = PA.sigma_and_gradient(lat_a, ka, checkpoint_every=ca)
+        torch.cuda.synchronize()
+        dta = reduce_max(dist, time.perf_counter() - t0, dev)
+        lat_a.close()
+        adjoint = {"value": ka / dta, "unit": "adjoint steps/s", "lattice": f"D2Q9 E8 {na}x{na} slab",
+                   "steps": ka, "checkpoint_every": ca, "seconds": dta,
+                   "mlups": na * na * ka / dta / 1e6, "precision": "fp32 forward, binary64 adjoint",
+                   "sigma": sig, "dsigma_dG": dGa,
+                   "accuracy": "FP32-forward gradient within 1e-3 of FP64 (tests/test_gpu_adjoint.py)"}
+
     # end to end through the C ABI with host buffers: create from the pinned
     # host density (H2D), K steps, read back the density (D2H) and the
     # observables
@@ -406,7 +429,7 @@ def run_gb300(args, dist, rank, ws):
                        "l2": "inputs larger than L2 (2 x 1.27 GB populations)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "fp64": fp64, "literal_g": lit, "fused_kernel": fused,
-            "batched_2d": batched,
+            "batched_2d": batched, "adjoint": adjoint,
             "observables": {"mass": obs["mass"], "umax": obs["umax"],
                             "rho_min": obs["rho_min"], "rho_max": obs["rho_max"],
                             "stable": stable, "first_unstable_step": obs["error_step"]},
@@ -425,6 +448,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-literal", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--size", type=int, default=256,
                     help="cube edge (default 256, the workload; smaller only for profiling)")
     args = ap.parse_args()
