@@ -241,6 +241,8 @@ def run_gb300(args, dist, rank, ws):
     lat = P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), L.E8_3D.bases,
                     L.E8_3D.weights, precision="fp32", tau=1.0, G=G, convention=CONVENTION,
                     stream=stream.cuda_stream)
+    if args.zchunk:
+        P.lb_set_option(lat.ctx, P.LB_OPT_ZCHUNK, args.zchunk)
     fused = P.lb_fused_active(lat.ctx)
     lat.step(args.warmup)
     lat.sync()
@@ -449,6 +451,8 @@ def main():
     ap.add_argument("--no-literal", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--zchunk", type=int, default=0,
+                    help="z planes per CTA of the fused kernel (default: the library's)")
     ap.add_argument("--size", type=int, default=256,
                     help="cube edge (default 256, the workload; smaller only for profiling)")
     args = ap.parse_args()
