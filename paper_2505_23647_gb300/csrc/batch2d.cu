@@ -2,19 +2,21 @@
 // lattice or for many independent lattices in one persistent launch.
 //
 // One launch = one step of every lattice it covers (eqs. lbm, omega_i, f_eq,
-// GuoForcing, sc_f).  A CTA owns a TX x TY tile: each thread pulls its
-// node's populations f_i(x) = A_i(x - xi_i), forms n and psi = exp(-1/n)
-// into a shared tile with a radius-2 halo (the halo's psi recomputed from
-// populations its neighbours read too, so those loads hit L2), then forms
-// the stencil force from the shared tile, collides and writes the node's
-// post-collision populations once.  Forcing stencils are any weights on the
-// 2D groups (1,0), (1,1), (2,0), (2,1), (2,2) (E4, E6, E8 and their tuned
-// variants), per lattice.
+// GuoForcing, sc_f).  The unit of work is one warp marching a 32-column
+// strip of a lattice over a chunk of rows (march below): each population is
+// read once per step in coalesced rows, psi is formed once per node plus four
+// halo columns, the stencil force is accumulated row by row in registers and
+// a row is collided and written as soon as the two rows above it are known.
+// Warps synchronise only with themselves, so there is no block-wide barrier
+// in the step.  Forcing stencils are any weights on the 2D groups (1,0),
+// (1,1), (2,0), (2,1), (2,2) (E4, E6, E8 and their tuned variants), per
+// lattice.
 //
-// Batches (lb_batch_*): the tiles of all lattices form one table; a grid
-// sized to the resident CTAs walks it, so boxes of uneven size share one
-// launch; K launches are captured into a CUDA graph and replayed.  The tile
-// shape is a template parameter picked per batch by lb_batch_tune.
+// Batches (lb_batch_*): the (lattice, strip, row chunk) items of all lattices
+// form one table walked by a grid of resident warps, so boxes of uneven size
+// share one launch; 64 launches are captured into a CUDA graph and replayed.
+// The row-chunk length is picked per batch by lb_batch_tune; it changes the
+// schedule only, never what a node computes.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -42,11 +44,12 @@ struct Inst {
     // 4/9, 1/9, 1/36; cw = (1 - 1/(2 tau)) w): omega w, -3 cw, 4.5 omega w,
     // 3 omega w, 9 cw, 3 cw
     float omw[3], m3cw[3], b45[3], d3[3], c9[3], c3[3];
-    int wide;           // 1 if a radius-2 group has a nonzero weight
+    float M1, M2;       // row sums of the weights at |d| = 1, 2 (M2 doubled)
 };
 
+// one work item of a batch: rows [y0, y1) of the strip [x0, x0 + 32) of lattice inst
 struct Tile {
-    int inst, x0, y0;
+    int inst, x0, y0, y1;
 };
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
@@ -102,133 +105,158 @@ __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, flo
 #undef SCLBM_PAIR9
 }
 
-// stencil force sums (eq. sc_f before the -G' psi(x) factor) from the
-// shared psi tile around pc (rows EX apart): per in-plane ring
-// k = |e|^2 the sums of e_x psi and e_y psi, taken as differences of
-// opposite nodes
-template <int EX>
-__device__ __forceinline__ void force2d(const float *pc, const Inst &I, float &Fx, float &Fy) {
-    auto P = [&](int dx, int dy) { return pc[dy * EX + dx]; };
-    const float X1 = P(1, 0) - P(-1, 0), Y1 = P(0, 1) - P(0, -1);
-    const float a = P(1, 1), b = P(1, -1), c = P(-1, 1), d = P(-1, -1);
-    const float X2 = (a - c) + (b - d), Y2 = (a - b) + (c - d);
-    Fx = fmaf(I.W[1], X2, I.W[0] * X1);
-    Fy = fmaf(I.W[1], Y2, I.W[0] * Y1);
-    if (I.wide) {
-        const float X4h = P(2, 0) - P(-2, 0), Y4h = P(0, 2) - P(0, -2);
-        const float p21 = P(2, 1), p2m = P(2, -1), m21 = P(-2, 1), m2m = P(-2, -1);
-        const float p12 = P(1, 2), p1m = P(1, -2), m12 = P(-1, 2), m1m = P(-1, -2);
-        const float X5 = fmaf(2.f, (p21 - m21) + (p2m - m2m), (p12 - m12) + (p1m - m1m));
-        const float Y5 = fmaf(2.f, (p12 - p1m) + (m12 - m1m), (p21 - p2m) + (m21 - m2m));
-        const float q1 = P(2, 2), q2 = P(2, -2), q3 = P(-2, 2), q4 = P(-2, -2);
-        const float X8h = (q1 - q3) + (q2 - q4), Y8h = (q1 - q2) + (q3 - q4);
-        Fx = fmaf(I.W2[2], X4h, Fx);
-        Fy = fmaf(I.W2[2], Y4h, Fy);
-        Fx = fmaf(I.W[3], X5, Fx);
-        Fy = fmaf(I.W[3], Y5, Fy);
-        Fx = fmaf(I.W2[4], X8h, Fx);
-        Fy = fmaf(I.W2[4], Y8h, Fy);
-    }
-}
-
-// halo node h (0 .. EXY - TX*TY - 1) of a TX x TY tile extended by R, in
-// extended coordinates: R full rows on top, the side columns, R rows below
-template <int TX, int TY>
-__device__ __forceinline__ void halo_xy(int h, int &hx, int &hy) {
-    constexpr int EX = TX + 2 * R;
-    constexpr int top = R * EX, sides = TY * 2 * R;
-    if (h < top) {
-        hy = h / EX;
-        hx = h % EX;
-    } else if (h < top + sides) {
-        const int k = h - top;
-        hy = R + k / (2 * R);
-        const int c = k % (2 * R);
-        hx = c < R ? c : TX + c;
-    } else {
-        const int k = h - top - sides;
-        hy = R + TY + k / EX;
-        hx = k % EX;
-    }
-}
-
-// One tile of one lattice; ps is the CTA's shared psi tile.  Tiles may run
-// past the lattice edge (sizes that are not multiples of the tile): those
-// threads work on the periodic image and store nothing.
-template <int TX, int TY>
-__device__ __forceinline__ void tile_step(const Inst &I, int x0, int y0, int parity, float *ps) {
-    constexpr int EX = TX + 2 * R, EY = TY + 2 * R, EXY = EX * EY, NT = TX * TY;
-    const int t = threadIdx.x, tx = t % TX, ty = t / TX;
+// One warp marches rows y0 - 2 .. y1 + 1 of the 32-column strip [x0, x0 + 32)
+// of lattice I and collides rows y0 .. y1 - 1.  Per row r: the lanes pull the
+// row's populations f_i(x, r) = A_i(x - xi_i, r - xi_iy) (coalesced rows),
+// form n and psi of their node (lanes 0..3 also of the halo columns x0 - 2,
+// x0 - 1, x0 + 32, x0 + 33) into the warp's row buffer, and add row r's share
+// of the force to the five target rows r - 2 .. r + 2 it touches: with
+// in-row sums X1 = psi(x+1) - psi(x-1), X2 = psi(x+2) - psi(x-2) and S1, S2
+// the pair sums relative to psi(x),
+//   F_x(t) += W(1+d^2) X1 + 2 W(4+d^2) X2,  F_y(t) += d (W(1+d^2) S1 + W(4+d^2) S2)
+// for d = r - t, plus (once per target) sum_d d M_d (psi(x, t+d) - psi(x, t-d))
+// with M_d = sum over the row of W(dx^2 + d^2) -- the exact form of eq. sc_f
+// for the 2D groups up to (2,2).  Row r - 2 is then complete: it is collided
+// from the populations the lane has held since it pulled them, and written.
+// Sizes that are not multiples of 32: lanes past the edge work on the
+// periodic image and store nothing.
+__device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int parity,
+                                      float *row, int lane) {
     const int nx = I.nx, ny = I.ny, N = nx * ny;
     const int cur = I.cur0 ^ parity;
     const float *__restrict__ A = I.f[cur];
     float *__restrict__ B = I.f[cur ^ 1];
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool owner = gx < nx && gy < ny;
-    const int x = gx % nx, y = gy % ny;
-    float g[9];
-    pull9(A, N, nx, ny, x, y, g);
-    const float dn = dens9(g);
-    const float n = dn + I.rho0;
-    const bool bad = owner && !(n > 0.f);
-    const float psi_c = fc::psi32(n);
-    ps[(ty + R) * EX + tx + R] = psi_c;
-    for (int h = t; h < EXY - NT; h += NT) {
-        int hx, hy;
-        halo_xy<TX, TY>(h, hx, hy);
-        int ax = (x0 + hx - R) % nx, ay = (y0 + hy - R) % ny;
-        ax += ax < 0 ? nx : 0;
-        ay += ay < 0 ? ny : 0;
-        float gh[9];
-        pull9(A, N, nx, ny, ax, ay, gh);
-        ps[hy * EX + hx] = fc::psi32(dens9(gh) + I.rho0);
-    }
-    __syncthreads();
-    if (owner) {
-        float Fx, Fy;
-        force2d<EX>(ps + (ty + R) * EX + tx + R, I, Fx, Fy);
-        const float pre = I.mGp * psi_c;
-        float out[9];
-        collide9(g, dn, pre * Fx, pre * Fy, I, out);
-        const long long s = (long long)y * nx + x;
+    const int gx = x0 + lane;
+    const bool xown = gx < nx;
+    const int x = gx % nx;
+    int hx = (lane < 2 ? x0 - 2 + lane : x0 + 30 + lane) % nx;
+    hx += hx < 0 ? nx : 0;
+    const int hpos = lane < 2 ? lane : lane + 32;
+    float gq[3][9], dq[3];
+    float ps[5], ax[5], ay[5];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B[(long long)i * N + s] = out[i];
+    for (int k = 0; k < 5; ++k) ps[k] = ax[k] = ay[k] = 0.f;
+    bool bad = false;
+    const int nit = (y1 - y0) + 4;
+    // the next row's populations are in flight while this row is computed
+    float gn[9], ghn[9];
+    auto row_of = [&](int it) {
+        int yr = (y0 - 2 + it) % ny;
+        return yr + (yr < 0 ? ny : 0);
+    };
+    pull9(A, N, nx, ny, x, row_of(0), gn);
+    if (lane < 4) pull9(A, N, nx, ny, hx, row_of(0), ghn);
+    for (int it = 0; it < nit; ++it) {
+        float gh[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            gq[2][i] = gn[i];
+            gh[i] = ghn[i];
+        }
+        if (it + 1 < nit) {
+            const int yn = row_of(it + 1);
+            pull9(A, N, nx, ny, x, yn, gn);
+            if (lane < 4) pull9(A, N, nx, ny, hx, yn, ghn);
+        }
+        dq[2] = dens9(gq[2]);
+        const float n = dq[2] + I.rho0;
+        bad |= xown && it >= 2 && it < nit - 2 && !(n > 0.f);
+        ps[4] = fc::psi32(n);
+        float psh = 0.f;
+        if (lane < 4) psh = fc::psi32(dens9(gh) + I.rho0);
+        __syncwarp();   // the previous row's readers are done
+        row[lane + 2] = ps[4];
+        if (lane < 4) row[hpos] = psh;
+        __syncwarp();
+        const float s0 = ps[4];
+        const float p1 = row[lane + 3], m1 = row[lane + 1], p2 = row[lane + 4], m2 = row[lane];
+        const float X1 = p1 - m1, X2 = p2 - m2;
+        const float S1 = (p1 - s0) + (m1 - s0), S2 = (p2 - s0) + (m2 - s0);
+        const float cx0 = fmaf(I.W2[2], X2, I.W[0] * X1);
+        const float cx1 = fmaf(I.W2[3], X2, I.W[1] * X1);
+        const float cx2 = fmaf(I.W2[4], X2, I.W[3] * X1);
+        const float cz1 = fmaf(I.W[3], S2, I.W[1] * S1);
+        const float cz2 = fmaf(I.W2[4], S2, I.W2[3] * S1);   // carries |d| = 2
+        ax[0] += cx2;
+        ay[0] += cz2;
+        ax[1] += cx1;
+        ay[1] += cz1;
+        ax[2] += cx0;
+        ax[3] += cx1;
+        ay[3] -= cz1;
+        ax[4] += cx2;
+        ay[4] -= cz2;
+        if (it >= 4) {   // row t = y0 - 4 + it is complete
+            const int t = y0 - 4 + it;
+            float fy = fmaf(I.M1, ps[3] - ps[1], ay[0]);
+            fy = fmaf(I.M2, ps[4] - ps[0], fy);
+            const float pre = I.mGp * ps[2];
+            float out[9];
+            collide9(gq[0], dq[0], pre * ax[0], pre * fy, I, out);
+            if (xown) {
+                const long long s = (long long)t * nx + x;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) B[(long long)i * N + s] = out[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ps[k] = ps[k + 1];
+            ax[k] = ax[k + 1];
+            ay[k] = ay[k + 1];
+        }
+        ax[4] = ay[4] = 0.f;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            dq[r] = dq[r + 1];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) gq[r][i] = gq[r + 1][i];
+        }
     }
     // n <= 0 or NaN: one report per warp, none once the step is recorded (an
     // unstable lattice must not turn every node into an atomic)
     const unsigned m = __ballot_sync(0xffffffffu, bad);
-    if (m && (t & 31) == __ffs(m) - 1) {
+    if (m && lane == __ffs(m) - 1) {
         const unsigned long long step = I.flags->step;
         if (I.flags->err_step > step) atomicMin(&I.flags->err_step, step);
     }
-    __syncthreads();   // the next tile reuses ps
 }
 
-// one lattice: one CTA per tile; the last CTA advances the step counter
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) k_fused2d(const Inst I, int parity) {
-    __shared__ float ps[(TX + 2 * R) * (TY + 2 * R)];
-    tile_step<TX, TY>(I, blockIdx.x * TX, blockIdx.y * TY, parity, ps);
+constexpr int WPB = 8;   // warps (strips) per block
+
+// one lattice: warp k of the grid marches strip k % nstrips, row chunk
+// k / nstrips; the last block advances the step counter
+__global__ void __launch_bounds__(WPB * 32, 2) k_strip2d(const Inst I, int rows, int parity) {
+    __shared__ float buf[WPB][32 + 2 * R];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nstrips = (I.nx + 31) / 32;
+    const int k = blockIdx.x * WPB + w;
+    const int y0 = (k / nstrips) * rows;
+    if (y0 < I.ny)
+        march(I, (k % nstrips) * 32, y0, min(y0 + rows, I.ny), parity, buf[w], lane);
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&I.flags->blocks_done, 1ULL) == (unsigned long long)gridDim.x * gridDim.y - 1) {
+        if (atomicAdd(&I.flags->blocks_done, 1ULL) == (unsigned long long)gridDim.x - 1) {
             I.flags->blocks_done = 0;
             I.flags->step = I.flags->step + 1;
         }
     }
 }
 
-// many lattices: a resident grid walks the tile table
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) k_fused2d_batch(const Inst *__restrict__ insts,
-                                                           const Tile *__restrict__ tiles,
-                                                           int ntiles, int ninst, int parity,
-                                                           unsigned long long *done) {
-    __shared__ float ps[(TX + 2 * R) * (TY + 2 * R)];
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        const Tile tl = tiles[k];
-        tile_step<TX, TY>(insts[tl.inst], tl.x0, tl.y0, parity, ps);
+// many lattices: a resident grid of warps walks the table of (lattice,
+// strip, row chunk) items; the last block advances every lattice's counter
+__global__ void __launch_bounds__(WPB * 32, 2) k_strip2d_batch(const Inst *__restrict__ insts,
+                                                            const Tile *__restrict__ items,
+                                                            int nitems, int ninst, int parity,
+                                                            unsigned long long *done) {
+    __shared__ float buf[WPB][32 + 2 * R];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = blockIdx.x * WPB + w; k < nitems; k += gridDim.x * WPB) {
+        const Tile it = items[k];
+        march(insts[it.inst], it.x0, it.y0, it.y1, parity, buf[w], lane);
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(done, 1ULL) == gridDim.x - 1) {
@@ -238,50 +266,32 @@ __global__ void __launch_bounds__(TX * TY) k_fused2d_batch(const Inst *__restric
     }
 }
 
-// tile shapes lb_batch_tune chooses from
+// work shapes lb_batch_tune chooses from: 32-column strips, row chunks of
+// SHAPE_TY rows (shorter chunks balance better, longer ones repeat fewer
+// warm-up rows)
 constexpr int NSHAPE = 5;
-constexpr int SHAPE_TX[NSHAPE] = {32, 64, 32, 16, 32};
-constexpr int SHAPE_TY[NSHAPE] = {8, 4, 16, 16, 4};
+constexpr int SHAPE_TX[NSHAPE] = {32, 32, 32, 32, 32};
+constexpr int SHAPE_TY[NSHAPE] = {16, 8, 32, 64, 128};
+constexpr int ROWS_ONE = 16;   // row chunk of a single lattice
 
-template <int S>
 void launch_one(const Inst &I, int parity, cudaStream_t st) {
-    constexpr int TX = SHAPE_TX[S], TY = SHAPE_TY[S];
-    dim3 grid((I.nx + TX - 1) / TX, (I.ny + TY - 1) / TY);
-    k_fused2d<TX, TY><<<grid, TX * TY, 0, st>>>(I, parity);
+    const int items = ((I.nx + 31) / 32) * ((I.ny + ROWS_ONE - 1) / ROWS_ONE);
+    k_strip2d<<<(items + WPB - 1) / WPB, WPB * 32, 0, st>>>(I, ROWS_ONE, parity);
 }
 
-template <int S>
-void launch_batch(const Inst *insts, const Tile *tiles, int ntiles, int ninst, int parity,
-                  unsigned long long *done, int grid, cudaStream_t st) {
-    constexpr int TX = SHAPE_TX[S], TY = SHAPE_TY[S];
-    k_fused2d_batch<TX, TY><<<grid, TX * TY, 0, st>>>(insts, tiles, ntiles, ninst, parity, done);
-}
-
-void launch_batch_shape(int s, const Inst *insts, const Tile *tiles, int ntiles, int ninst,
+void launch_batch_shape(int, const Inst *insts, const Tile *items, int nitems, int ninst,
                         int parity, unsigned long long *done, int grid, cudaStream_t st) {
-    switch (s) {
-        case 0: launch_batch<0>(insts, tiles, ntiles, ninst, parity, done, grid, st); break;
-        case 1: launch_batch<1>(insts, tiles, ntiles, ninst, parity, done, grid, st); break;
-        case 2: launch_batch<2>(insts, tiles, ntiles, ninst, parity, done, grid, st); break;
-        case 3: launch_batch<3>(insts, tiles, ntiles, ninst, parity, done, grid, st); break;
-        default: launch_batch<4>(insts, tiles, ntiles, ninst, parity, done, grid, st); break;
-    }
+    k_strip2d_batch<<<grid, WPB * 32, 0, st>>>(insts, items, nitems, ninst, parity, done);
 }
 
-int resident_grid(int s) {
+// blocks of the batch kernel resident on the whole GPU
+int resident_grid(int) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int threads = SHAPE_TX[s] * SHAPE_TY[s];
-    cudaError_t e = cudaSuccess;
-    switch (s) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused2d_batch<32, 8>, threads, 0); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused2d_batch<64, 4>, threads, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused2d_batch<32, 16>, threads, 0); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused2d_batch<16, 16>, threads, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused2d_batch<32, 4>, threads, 0); break;
-    }
-    if (e != cudaSuccess || per < 1) per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_strip2d_batch, WPB * 32, 0) !=
+            cudaSuccess || per < 1)
+        per = 1;
     return (sms > 0 ? sms : 1) * per;
 }
 
@@ -319,7 +329,12 @@ static void inst_from_ctx(const lb_ctx *c, b2::Inst *I) {
         I->W[q] = c->fused2d_W[q];
         I->W2[q] = 2.f * c->fused2d_W[q];
     }
-    I->wide = (c->fused2d_W[2] != 0.f || c->fused2d_W[3] != 0.f || c->fused2d_W[4] != 0.f) ? 1 : 0;
+    {   // M_d = sum over dx of W(dx^2 + d^2): W(1) + 2 W(2) + 2 W(5), W(4) + 2 W(5) + 2 W(8)
+        const double w0 = c->fused2d_W[0], w1 = c->fused2d_W[1], w2 = c->fused2d_W[2];
+        const double w3 = c->fused2d_W[3], w4 = c->fused2d_W[4];
+        I->M1 = (float)(w0 + 2.0 * w1 + 2.0 * w3);
+        I->M2 = (float)(2.0 * (w2 + 2.0 * w3 + 2.0 * w4));
+    }
     const double om = c->k.omega;
     I->mGp = (float)c->k.mGp;
     I->rho0 = (float)c->k.rho0;
@@ -342,7 +357,7 @@ cudaError_t f32_fused2d_step(lb_ctx *c) {
     inst_from_ctx(c, &I);
     I.cur0 = 0;
     tm_begin(c, LB_KERNEL_FUSED);
-    b2::launch_one<0>(I, c->cur, c->stream);
+    b2::launch_one(I, c->cur, c->stream);
     tm_end(c);
     c->launches += 1;
     c->cur = 1 - c->cur;
@@ -388,16 +403,19 @@ lb_status ensure_tiles(lb_batch *b, int s) {
     if (b->d_tiles[s]) return LB_OK;
     const int TX = b2::SHAPE_TX[s], TY = b2::SHAPE_TY[s];
     std::vector<b2::Tile> t;
+    // lattice by lattice, row chunk by row chunk, strips side by side: warps
+    // running at the same time share their halo columns in L2
     for (int i = 0; i < (int)b->ctx.size(); ++i)
         for (int y0 = 0; y0 < b->inst[i].ny; y0 += TY)
-            for (int x0 = 0; x0 < b->inst[i].nx; x0 += TX) t.push_back({i, x0, y0});
+            for (int x0 = 0; x0 < b->inst[i].nx; x0 += TX)
+                t.push_back({i, x0, y0, y0 + TY < b->inst[i].ny ? y0 + TY : b->inst[i].ny});
     cudaError_t e = cudaMalloc(&b->d_tiles[s], t.size() * sizeof(b2::Tile));
     if (e != cudaSuccess) return bfail(e, "lb_batch tile table");
     e = cudaMemcpy(b->d_tiles[s], t.data(), t.size() * sizeof(b2::Tile), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bfail(e, "lb_batch tile table");
     b->ntiles[s] = (int)t.size();
-    const int g = b2::resident_grid(s);
-    b->grid[s] = g < b->ntiles[s] ? g : b->ntiles[s];
+    const int g = b2::resident_grid(s), need = (b->ntiles[s] + b2::WPB - 1) / b2::WPB;
+    b->grid[s] = g < need ? g : need;
     return LB_OK;
 }
 
