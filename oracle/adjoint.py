@@ -181,3 +181,21 @@ def gradient(o, g0, steps, n_interfaces):
         dW += w_s
         dGp += g_s
     return sigma, lam, dW, dGp
+
+
+def gradient_of_density_functional(o, g0, steps, fn):
+    """A loss fn(n) -> (L, dL/dn) of the density after `steps` steps from g0
+    and its gradient (forward in numpy, then the adjoint steps backwards):
+    returns (L, dL/dg0, dL/dW per group, dL/dG')."""
+    states = [g0]
+    for _ in range(steps):
+        states.append(step_forward(o, states[-1]))
+    value, dn = fn(states[-1].sum(axis=0))
+    lam = np.broadcast_to(dn, states[-1].shape).copy()
+    dW = np.zeros(len(o.groups))
+    dGp = 0.0
+    for s in range(steps - 1, -1, -1):
+        lam, w_s, g_s = step_adjoint(o, states[s], lam)
+        dW += w_s
+        dGp += g_s
+    return value, lam, dW, dGp

@@ -95,6 +95,62 @@ def sigma_and_gradient(lattice, steps, checkpoint_every=100, n_interfaces=2):
     return sigma, dW, dG, lam0
 
 
+def density_functional_and_gradient(lattice, steps, fn, checkpoint_every=100):
+    """A loss L(n) of the density after ``steps`` steps and its gradient with
+    respect to the stencil group weights, G and the initial state.  ``fn(n)``
+    receives the final density (shape of ``lattice.shape``) and returns
+    (L, dL/dn); since n = sum_i f_i, dL/df_i = dL/dn seeds the adjoint.
+    Returns (L, dW [groups], dG, dL/d(initial state))."""
+    K = max(1, int(checkpoint_every))
+    ckpts = []
+    done = 0
+    while done < steps:
+        ckpts.append((done, lattice.state()))
+        k = min(K, steps - done)
+        lattice.step(k)
+        done += k
+    n, _ = lattice.fields()
+    value, dn = fn(n)
+    adj = Adjoint(lattice)
+    try:
+        adj.set(np.broadcast_to(np.asarray(dn, dtype=np.float64), (lattice.Q,) + lattice.shape))
+        for start, st in reversed(ckpts):
+            lattice.set_state(st)
+            adj.run(min(K, steps - start))
+        dW, dG = adj.gradient()
+        lam0 = adj.get()
+    finally:
+        adj.close()
+    return value, dW, dG, lam0
+
+
+def density_ratio(x_liquid, x_gas):
+    """L(n) = n_l / n_g of a flat slab (gradients along x): the densities are
+    the y (and z) averages of columns x_liquid and x_gas."""
+    def fn(n):
+        cols = n.shape[0] * n.shape[1]
+        nl, ng = n[..., x_liquid].mean(), n[..., x_gas].mean()
+        d = np.zeros_like(n)
+        d[..., x_liquid] = 1.0 / (ng * cols)
+        d[..., x_gas] = -nl / (ng * ng * cols)
+        return nl / ng, d
+    return fn
+
+
+def interface_width(n_liquid, n_gas, n_interfaces=2):
+    """Smooth width of the interfaces of a flat slab (gradients along x):
+    L(n) = 6 sum_x (n(x) - n_g)(n_l - n(x)) / (n_l - n_g)^2 / #interfaces with
+    n(x) the y (and z) average; for a tanh profile of width w it equals w."""
+    def fn(n):
+        cols = n.shape[0] * n.shape[1]
+        prof = n.mean(axis=(0, 1))
+        dl = n_liquid - n_gas
+        val = 6.0 * float(np.sum((prof - n_gas) * (n_liquid - prof))) / (dl * dl) / n_interfaces
+        dprof = 6.0 * (n_liquid + n_gas - 2.0 * prof) / (dl * dl) / n_interfaces
+        return val, np.broadcast_to(dprof / cols, n.shape).copy()
+    return fn
+
+
 _FN = None
 
 
@@ -140,4 +196,5 @@ def flat_sigma(W, G, spec):
     return _torch_function().apply(W, G, spec)
 
 
-__all__ = ["Adjoint", "sigma_and_gradient", "flat_sigma", "LbError"]
+__all__ = ["Adjoint", "sigma_and_gradient", "density_functional_and_gradient", "density_ratio",
+           "interface_width", "flat_sigma", "LbError"]

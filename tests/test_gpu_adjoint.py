@@ -2,7 +2,8 @@
 (oracle/adjoint.py, itself pinned to central finite differences of the
 oracle's forward step) and against finite differences of the GPU's own
 forward runs; checkpointing changes nothing; the torch.autograd.Function
-returns the same gradient; and a gradient solve of the paper's surface
+returns the same gradient; losses on the density (liquid/gas density ratio,
+interface width) differentiate the same way; and a gradient solve of the paper's surface
 tension knob (Table tab:e4_tuning_6, sigma0_hat) hits a target sigma_0."""
 from fractions import Fraction as Fr
 
@@ -159,3 +160,67 @@ def test_gradient_solve_hits_target_sigma():
             break
         s0 -= (sigma - target) / dsig
     assert abs(sigma / target - 1.0) < 1e-3, (s0, sigma, target)
+
+
+def _oracle_width(nl, ng):
+    """6 sum (n - ng)(nl - n) / (nl - ng)^2 / 2 of the column-averaged profile."""
+    def fn(n):
+        cols = n.shape[0] * n.shape[1]
+        prof = n.mean(axis=(0, 1))
+        d2 = (nl - ng) ** 2
+        val = 3.0 * float(np.sum((prof - ng) * (nl - prof))) / d2
+        return val, np.broadcast_to(3.0 * (nl + ng - 2 * prof) / d2 / cols, n.shape).copy()
+    return fn
+
+
+def _oracle_ratio(xl, xg):
+    """n_l / n_g of the column averages at xl (liquid) and xg (gas)."""
+    def fn(n):
+        cols = n.shape[0] * n.shape[1]
+        nl, ng = n[..., xl].mean(), n[..., xg].mean()
+        d = np.zeros_like(n)
+        d[..., xl] = 1.0 / (ng * cols)
+        d[..., xg] = -nl / (ng * ng * cols)
+        return nl / ng, d
+    return fn
+
+
+@pytest.mark.parametrize("which", ["ratio", "width"])
+def test_density_functionals_match_oracle_adjoint(which):
+    lattice, shape, st, tau, G, conv, eps, steps = CASES[0]
+    nx, ny = shape
+    if which == "ratio":
+        fn_gpu, fn_or = AD.density_ratio(nx // 2, 1), _oracle_ratio(nx // 2, 1)
+    else:
+        fn_gpu, fn_or = AD.interface_width(N_LIQ, N_GAS), _oracle_width(N_LIQ, N_GAS)
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    g0 = lat.state()
+    val, dW, dG, lam0 = AD.density_functional_and_gradient(lat, steps, fn_gpu, checkpoint_every=5)
+    lat.close()
+    o = oracle.Oracle(lattice, (1, ny, nx), st.groups, tau=tau, G=G, convention=conv)
+    v_o, lam_o, dW_o, dGp_o = OAD.gradient_of_density_functional(o, g0.reshape((9, 1, ny, nx)), steps,
+                                                                   fn_or)
+    assert abs(val - v_o) < 1e-12 * abs(v_o)
+    assert _rel(dW, dW_o) < 1e-10 and abs(dG - dGp_o) < 1e-10 * abs(dGp_o)
+    assert _rel(lam0.reshape(lam_o.shape), lam_o) < 1e-10
+
+
+def test_interface_width_gradient_matches_gpu_finite_differences():
+    lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
+    steps = 150
+    fn = AD.interface_width(N_LIQ, N_GAS)
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    w, dW, dG, _ = AD.density_functional_and_gradient(lat, steps, fn, checkpoint_every=40)
+    lat.close()
+    assert 1.0 < w < 10.0
+
+    def width_of(Gv):
+        l = _lat(lattice, shape, st, tau, Gv, conv, eps)
+        l.step(steps)
+        n, _ = l.fields()
+        l.close()
+        return fn(n)[0]
+
+    h = 1e-6 * abs(G)
+    fd = (width_of(G + h) - width_of(G - h)) / (2 * h)
+    assert abs(dG - fd) < 1e-6 * abs(fd) + 1e-9, (dG, fd)

@@ -84,3 +84,45 @@ def test_adjoint_gradient_matches_finite_differences(lattice, shape, st, tau, G,
         fd = (_sigma_after(lattice, shape, st.groups, tau, G, conv, gp, steps) -
               _sigma_after(lattice, shape, st.groups, tau, G, conv, gm, steps)) / (2 * h)
         assert abs(lam[idx] - fd) < 1e-6 * abs(fd) + 1e-10, (idx, lam[idx], fd)
+
+
+def _ratio_fn(xl, xg):
+    """n_l / n_g of the column averages at xl (liquid) and xg (gas)."""
+    def fn(n):
+        cols = n.shape[0] * n.shape[1]
+        nl, ng = n[..., xl].mean(), n[..., xg].mean()
+        d = np.zeros_like(n)
+        d[..., xl] = 1.0 / (ng * cols)
+        d[..., xg] = -nl / (ng * ng * cols)
+        return nl / ng, d
+    return fn
+
+
+def _n_after(lattice, shape, groups, tau, G, conv, g0, steps):
+    o = oracle.Oracle(lattice, shape, groups, tau=tau, G=G, convention=conv)
+    o.f = g0.copy()
+    o.step(steps)
+    return o.fields()["n"]
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,steps", CASES[:2])
+def test_density_functional_gradient_matches_finite_differences(lattice, shape, st, tau, G, conv, steps):
+    """The same adjoint seeded by a loss on the density (the ratio of the
+    liquid to the gas column density) against central differences."""
+    o = _setup(lattice, shape, st, tau, G, conv)
+    g0 = o.f.copy()
+    nx = shape[2]
+    fn = _ratio_fn(nx // 2, 1)
+    val, lam, dW, dGp = AD.gradient_of_density_functional(o, g0, steps, fn)
+    assert abs(val - fn(_n_after(lattice, shape, st.groups, tau, G, conv, g0, steps))[0]) < 1e-12
+    for q, (b, wq) in enumerate(st.groups):
+        h = 1e-6 * float(wq)
+        gp = [(bb, float(ww) + (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        gm = [(bb, float(ww) - (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        fd = (fn(_n_after(lattice, shape, gp, tau, G, conv, g0, steps))[0] -
+              fn(_n_after(lattice, shape, gm, tau, G, conv, g0, steps))[0]) / (2 * h)
+        assert abs(dW[q] - fd) < 1e-6 * abs(fd) + 1e-9, (q, dW[q], fd)
+    h = 1e-6 * abs(G)
+    fd = (fn(_n_after(lattice, shape, st.groups, tau, G + h, conv, g0, steps))[0] -
+          fn(_n_after(lattice, shape, st.groups, tau, G - h, conv, g0, steps))[0]) / (2 * h)
+    assert abs(dGp - fd) < 1e-6 * abs(fd) + 1e-9
