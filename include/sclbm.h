@@ -339,6 +339,16 @@ lb_status lb_adjoint_zero_grad(lb_adjoint *adj);
  * dsigma/d(state) and adds sigma's explicit dependence on W and G to the
  * gradients. */
 lb_status lb_adjoint_seed_sigma(lb_adjoint *adj, int n_interfaces, double *sigma);
+/* Add the gradient of L_m = sum_x m(x) (P_xx - P_yy)(x) to lam, for site
+ * weights m (host array [N], the layout of one field of lb_get_fields): the
+ * normal minus a tangential component of the lattice pressure tensor of a
+ * slab with gradients along x (Appendices E/F; the ideal part cancels).
+ * Writes *value = L_m (may be NULL) and adds L_m's explicit dependence on W
+ * and G to the gradients.  Used with lb_adjoint_set for losses built from
+ * the density and the tensor together, e.g. the Tolman length
+ * z_e - z_s of a flat interface.  LB_EUNSUPPORTED for stencil groups
+ * outside Appendices E/F. */
+lb_status lb_adjoint_seed_pt(lb_adjoint *adj, const double *m, double *value);
 /* Carry lam back over the next nsteps steps of the context (see above). */
 lb_status lb_adjoint_run(lb_adjoint *adj, int nsteps);
 /* dL/dW per stencil group (n_groups doubles, may be NULL) and dL/dG. */

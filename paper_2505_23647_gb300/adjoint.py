@@ -44,6 +44,15 @@ class Adjoint:
                "lb_adjoint_seed_sigma")
         return s.value
 
+    def seed_pt(self, m):
+        """Add the gradient of sum_x m(x) (P_xx - P_yy)(x) to lam; returns the sum."""
+        m = np.ascontiguousarray(m, dtype=np.float64).reshape(-1)
+        if m.size != self.lat.N:
+            raise ValueError("m must have N entries")
+        v = ctypes.c_double(0.0)
+        _check(_lib.lb_adjoint_seed_pt(_vp(self.a), _ptr(m), ctypes.byref(v)), "lb_adjoint_seed_pt")
+        return v.value
+
     def run(self, nsteps):
         _check(_lib.lb_adjoint_run(_vp(self.a), int(nsteps)), "lb_adjoint_run")
 
@@ -151,6 +160,103 @@ def interface_width(n_liquid, n_gas, n_interfaces=2):
     return fn
 
 
+def _windows(prof):
+    """Interface windows of a periodic profile: for each crossing of the mid
+    density between x and x+1, the columns from half way to the previous
+    crossing to half way to the next one; +1 for gas -> liquid along +x."""
+    L = len(prof)
+    mid = 0.5 * (prof.max() + prof.min())
+    sg = np.sign(prof - mid)
+    cross = [(i, 1 if sg[(i + 1) % L] > sg[i] else -1) for i in range(L)
+             if sg[i] != sg[(i + 1) % L] and sg[i] != 0 and sg[(i + 1) % L] != 0]
+    out = []
+    k = len(cross)
+    for q, (i, d) in enumerate(cross):
+        gp = (i - cross[q - 1][0]) % L if k > 1 else L
+        gn = (cross[(q + 1) % k][0] - i) % L if k > 1 else L
+        out.append((i - gp // 2 + 1, i + gn // 2, d))
+    return out
+
+
+def tolman_and_gradient(lattice, steps, checkpoint_every=100):
+    """Tolman length delta = z_e - z_s of a flat slab (gradients along x) after
+    ``steps`` steps, averaged over its interfaces, and its gradient with
+    respect to the stencil group weights, G and the initial state.
+
+    Per interface window (columns a..b, site x the cell [x - 1/2, x + 1/2]):
+    z_s = sum x (P_N - P_T) / sum (P_N - P_T) from the lattice pressure tensor
+    (Appendices E/F), z_e the equimolar position from the window-end
+    densities, delta oriented from liquid to gas (eqs. zemzs, SCTolmanFlat).
+    The loss is a function of the column-averaged density and of
+    P_N - P_T: its density part seeds lam, its tensor part enters through
+    lb_adjoint_seed_pt.  Returns (delta, dW, dG, d delta/d(initial state))."""
+    K = max(1, int(checkpoint_every))
+    ckpts = []
+    done = 0
+    while done < steps:
+        ckpts.append((done, lattice.state()))
+        k = min(K, steps - done)
+        lattice.step(k)
+        done += k
+    n, _ = lattice.fields()
+    P = lattice.pressure_tensor()
+    D = P[0] - (P[2] if lattice.D == 2 else P[3])
+    cols = n.shape[0] * n.shape[1]
+    prof, dprof = n.mean(axis=(0, 1)), D.mean(axis=(0, 1))
+    L = len(prof)
+    wins = _windows(prof)
+    if not wins:
+        raise ValueError("no interface in the final state")
+    g_n = np.zeros(L)     # d delta / d profile
+    g_d = np.zeros(L)     # d delta / d (P_N - P_T) profile
+    delta = 0.0
+    for a, b, d in wins:
+        xs = np.arange(a, b + 1)
+        idx = xs % L
+        J = len(idx)
+        S = float(np.sum(dprof[idx]))
+        zs = float(np.sum(xs * dprof[idx])) / S
+        nv = prof[idx]
+        if d > 0:      # gas at a, liquid at b
+            T = float(np.sum(nv)) - J * nv[0]
+            Dl = nv[-1] - nv[0]
+            ze = (b + 0.5) - T / Dl
+            dT = np.ones(J)
+            dT[0] -= J
+            dD = np.zeros(J)
+            dD[-1], dD[0] = 1.0, -1.0
+            dze = -(dT * Dl - T * dD) / (Dl * Dl)
+        else:          # liquid at a, gas at b
+            T = float(np.sum(nv)) - J * nv[-1]
+            Dl = nv[0] - nv[-1]
+            ze = (a - 0.5) + T / Dl
+            dT = np.ones(J)
+            dT[-1] -= J
+            dD = np.zeros(J)
+            dD[0], dD[-1] = 1.0, -1.0
+            dze = (dT * Dl - T * dD) / (Dl * Dl)
+        orient = -d
+        delta += orient * (ze - zs)
+        np.add.at(g_n, idx, orient * dze)
+        np.add.at(g_d, idx, -orient * (xs - zs) / S)
+    nw = len(wins)
+    delta /= nw
+    g_n /= nw * cols
+    g_d /= nw * cols
+    adj = Adjoint(lattice)
+    try:
+        adj.set(np.broadcast_to(g_n, (lattice.Q,) + lattice.shape))
+        adj.seed_pt(np.broadcast_to(g_d, lattice.shape))
+        for start, st in reversed(ckpts):
+            lattice.set_state(st)
+            adj.run(min(K, steps - start))
+        dW, dG = adj.gradient()
+        lam0 = adj.get()
+    finally:
+        adj.close()
+    return delta, dW, dG, lam0
+
+
 _FN = None
 
 
@@ -197,4 +303,4 @@ def flat_sigma(W, G, spec):
 
 
 __all__ = ["Adjoint", "sigma_and_gradient", "density_functional_and_gradient", "density_ratio",
-           "interface_width", "flat_sigma", "LbError"]
+           "interface_width", "tolman_and_gradient", "flat_sigma", "LbError"]

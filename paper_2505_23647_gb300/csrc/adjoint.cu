@@ -231,6 +231,54 @@ __global__ void k_rowsum(const double *__restrict__ a, long long N, int chunks, 
     if (threadIdx.x == 0) out[row * chunks + ch] = sh[0];
 }
 
+// L = sum_x m(x) (P_xx - P_yy)(x) for given site weights m (the normal and a
+// tangential component of the Appendix E/F tensor of a slab with gradients
+// along x; n/3 cancels).  Per site x and pair (e, -e), with k = e_x^2 - e_y^2,
+// the tensor adds W k (kA psi(x)(psi(x+e) + psi(x-e)) + kB sum_l psi(x+q0) psi(x+q1)),
+// so dL/dpsi(y) gathers, over the pair's links through y,
+//   W k kA (m(y)(psi(y+e) + psi(y-e)) + m(y-e) psi(y-e) + m(y+e) psi(y+e))
+//   + W k kB sum_l (m(y-q0) psi(y-q0+q1) + m(y-q1) psi(y-q1+q0)).
+// lam_i(y) += psi'(n) dL/dpsi(y); the site's own terms give L (snode) and
+// dL/dW (gnode); dL/dG' = L/G' (every term carries G').
+template <int D, int Q>
+__global__ void k_seed_pt(const double *__restrict__ psi, const double *__restrict__ dpsi,
+                          const double *__restrict__ m, Geom g, const PTPairs P, const PairGroups PG,
+                          double *__restrict__ lam, double *__restrict__ gnode,
+                          double *__restrict__ snode) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        int x, y, z;
+        coords(g, s, x, y, z);
+        const double p0 = psi[s], m0 = m[s];
+        double gp = 0.0, own = 0.0;
+        for (int a = 0; a < P.npairs; ++a) {
+            const int e0 = P.v[a][0], e1 = P.v[a][1], e2 = P.v[a][2];
+            const double kk = (double)(e0 * e0 - e1 * e1);
+            if (kk == 0.0) continue;
+            const long long sp = site(g, x + e0, y + e1, z + e2), sm = site(g, x - e0, y - e1, z - e2);
+            const double wa = P.w[a] * kk;
+            double t = P.kA[a] * (m0 * (psi[sp] + psi[sm]) + m[sm] * psi[sm] + m[sp] * psi[sp]);
+            double Bown = 0.0;
+            for (int l = 0; l < P.nlink[a]; ++l) {
+                const signed char *q = &P.link[a][l][0][0];
+                const long long s0 = site(g, x - q[0], y - q[1], z - q[2]);
+                const long long s1 = site(g, x - q[3], y - q[4], z - q[5]);
+                t += P.kB[a] * (m[s0] * psi[site(g, x - q[0] + q[3], y - q[1] + q[4], z - q[2] + q[5])] +
+                                m[s1] * psi[site(g, x - q[3] + q[0], y - q[4] + q[1], z - q[5] + q[2])]);
+                Bown += psi[site(g, x + q[0], y + q[1], z + q[2])] * psi[site(g, x + q[3], y + q[4], z + q[5])];
+            }
+            gp += wa * t;
+            const double c = m0 * kk * (P.kA[a] * p0 * (psi[sp] + psi[sm]) + P.kB[a] * Bown);
+            own += P.w[a] * c;
+            gnode[(long long)PG.g[a] * g.N + s] += c;
+        }
+        snode[s] = own;
+        const double add = dpsi[s] * gp;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lam[(long long)i * g.N + s] += add;
+    }
+}
+
 }  // namespace adj
 }  // namespace sclbm
 
@@ -414,6 +462,44 @@ lb_status lb_adjoint_seed_sigma(lb_adjoint *a, int n_interfaces, double *sigma) 
     const double sig = 0.5 * c->Gp * inv * tot;
     a->dGp_direct += c->Gp != 0.0 ? sig / c->Gp : 0.0;
     if (sigma) *sigma = sig;
+    return LB_OK;
+}
+
+lb_status lb_adjoint_seed_pt(lb_adjoint *a, const double *m, double *value) {
+    if (!a || !m) return LB_EINVAL;
+    lb_ctx *c = a->c;
+    static PTPairs P;   // host staging (large); calls are serialised per adjoint
+    if (!build_pt_pairs(c, &P)) return LB_EUNSUPPORTED;
+    const long long N = a->g.N;
+    double *dm = nullptr;
+    cudaError_t e = cudaMalloc(&dm, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dm, m, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = c->p.precision == LB_FP64 ? f64_get_state(c, a->lam2) : f32_get_state(c, a->lam2);
+    if (e != cudaSuccess) {
+        cudaFree(dm);
+        return afail(e, "lb_adjoint_seed_pt");
+    }
+    lb_status s = fields_of(a, a->lam2);
+    if (s != LB_OK) {
+        cudaFree(dm);
+        return s;
+    }
+    const int gb = grid_for(N);
+    if (a->D == 2)
+        adj::k_seed_pt<2, 9><<<gb, 256, 0, c->stream>>>(a->psi, a->dpsi, dm, a->g, P, a->pg, a->lam,
+                                                      a->gnode, a->snode);
+    else
+        adj::k_seed_pt<3, 19><<<gb, 256, 0, c->stream>>>(a->psi, a->dpsi, dm, a->g, P, a->pg, a->lam,
+                                                       a->gnode, a->snode);
+    e = cudaGetLastError();
+    double tot = 0.0;
+    if (e == cudaSuccess) s = rowsums(a, a->snode, 1, &tot);
+    cudaFree(dm);
+    if (e != cudaSuccess) return afail(e, "lb_adjoint_seed_pt");
+    if (s != LB_OK) return s;
+    a->dGp_direct += c->Gp != 0.0 ? tot / c->Gp : 0.0;
+    if (value) *value = tot;
     return LB_OK;
 }
 

@@ -215,16 +215,6 @@ cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double
 // ---------------------------------------------------------------------------
 // Lattice pressure tensor.  Per pair e (with -e): the endpoint products
 // A = psi(x) (psi(x+e) + psi(x-e)) and the interior/midpoint link products
-// B = sum_links psi(x+a) psi(x+b) (links and order prepared on the host),
-// s = W (kA A + kB B), P^{mu nu} += s e^mu e^nu, starting from (n/3) delta.
-struct PTPairs {
-    int npairs;
-    signed char v[MAXP][3];
-    signed char nlink[MAXP];
-    signed char link[MAXP][4][2][3];
-    double w[MAXP], kA[MAXP], kB[MAXP];
-};
-
 template <int D>
 __global__ void __launch_bounds__(128) k_ptensor(Geom g, const double *__restrict__ n,
                                                  const double *__restrict__ psi, const PTPairs P,
@@ -272,7 +262,7 @@ static int igcd(int a, int b) {
 
 // Host: classify pairs and build the link lists (returns false for a group
 // outside Appendices E/F).
-static bool build_pt_pairs(const lb_ctx *c, PTPairs *P) {
+bool build_pt_pairs(const lb_ctx *c, PTPairs *P) {
     P->npairs = c->pairs64.npairs;
     for (int a = 0; a < P->npairs; ++a) {
         int e[3] = {c->pairs64.v[a][0], c->pairs64.v[a][1], c->pairs64.v[a][2]};

@@ -139,6 +139,19 @@ cudaError_t ghosts_refresh(lb_ctx *c);   // padded layouts: refresh ghost cells 
 cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
                        double *out_host9);
 cudaError_t ptensor(lb_ctx *c, const double *n, const double *psi, double *out);
+// lattice pressure tensor of Appendices E/F, per pair (e, -e): A = psi(x) (psi(x+e) +
+// psi(x-e)), B = sum over the pair's links of psi(x+a) psi(x+b) (links prepared
+// on the host), s = W (kA A + kB B), P^{mu nu}(x) += s e^mu e^nu, from (n/3) delta
+struct PTPairs {
+    int npairs;
+    signed char v[MAXP][3];
+    signed char nlink[MAXP];
+    signed char link[MAXP][4][2][3];
+    double w[MAXP], kA[MAXP], kB[MAXP];
+};
+// classify the context's pairs and build their link lists (false: a group
+// outside Appendices E/F)
+bool build_pt_pairs(const lb_ctx *c, PTPairs *P);
 cudaError_t exp_batch(const double *x, double *y, long long n,
                       unsigned long long *amb, cudaStream_t s);
 cudaError_t psi_batch(const double *n_in, double *psi, long long n, int kind, double eps,

@@ -224,3 +224,51 @@ def test_interface_width_gradient_matches_gpu_finite_differences():
     h = 1e-6 * abs(G)
     fd = (width_of(G + h) - width_of(G - h)) / (2 * h)
     assert abs(dG - fd) < 1e-6 * abs(fd) + 1e-9, (dG, fd)
+
+
+def _oracle_delta(lattice, shape, groups, tau, G, conv, g0, steps):
+    """Mean Tolman length of the oracle run, by the oracle's own analysis."""
+    from oracle import analysis as OA
+    nx, ny = shape[0], shape[1]
+    nz = shape[2] if len(shape) > 2 else 1
+    o = oracle.Oracle(lattice, (nz, ny, nx), groups, tau=tau, G=G, convention=conv)
+    o.f = g0.reshape((o.Q, nz, ny, nx)).copy()
+    o.step(steps)
+    obs = OA.flat_observables(o.pressure_tensor(), o.fields()["n"], D=o.D)
+    return float(np.mean([r["delta"] for r in obs]))
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_tolman_gradient_matches_oracle_finite_differences(case):
+    """delta = z_e - z_s (eqs. zemzs, SCTolmanFlat) through the adjoint: its
+    value equals the oracle's analysis of the oracle run, its gradient central
+    differences of that (weights per group, G, initial populations)."""
+    lattice, shape, st, tau, G, conv, eps, steps = CASES[case]
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    g0 = lat.state()
+    delta, dW, dG, lam0 = AD.tolman_and_gradient(lat, steps, checkpoint_every=5)
+    lat.close()
+    ref = _oracle_delta(lattice, shape, st.groups, tau, G, conv, g0, steps)
+    assert abs(delta - ref) < 1e-10 * abs(ref), (delta, ref)
+    for q, (b, wq) in enumerate(st.groups):
+        h = 1e-6 * float(wq)
+        gp = [(bb, float(ww) + (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        gm = [(bb, float(ww) - (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        fd = (_oracle_delta(lattice, shape, gp, tau, G, conv, g0, steps) -
+              _oracle_delta(lattice, shape, gm, tau, G, conv, g0, steps)) / (2 * h)
+        assert abs(dW[q] - fd) < 1e-5 * abs(fd) + 1e-7, (q, dW[q], fd)
+    h = 1e-6 * abs(G)
+    fd = (_oracle_delta(lattice, shape, st.groups, tau, G + h, conv, g0, steps) -
+          _oracle_delta(lattice, shape, st.groups, tau, G - h, conv, g0, steps)) / (2 * h)
+    assert abs(dG - fd) < 1e-5 * abs(fd) + 1e-7, (dG, fd)
+    rng = np.random.default_rng(2)
+    lam = lam0.reshape(g0.shape)
+    for _ in range(3):
+        idx = tuple(int(rng.integers(0, s)) for s in g0.shape)
+        h = 1e-4 * abs(g0[idx])
+        gp, gm = g0.copy(), g0.copy()
+        gp[idx] += h
+        gm[idx] -= h
+        fd = (_oracle_delta(lattice, shape, st.groups, tau, G, conv, gp, steps) -
+              _oracle_delta(lattice, shape, st.groups, tau, G, conv, gm, steps)) / (2 * h)
+        assert abs(lam[idx] - fd) < 1e-5 * abs(fd) + 1e-8, (idx, lam[idx], fd)
