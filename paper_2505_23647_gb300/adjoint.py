@@ -257,6 +257,64 @@ def tolman_and_gradient(lattice, steps, checkpoint_every=100):
     return delta, dW, dG, lam0
 
 
+def slab_observables(make_lattice, steps, x_liquid, x_gas, n_liquid, n_gas, checkpoint_every=100):
+    """The four quantities the stencil tuning of Sec. V targets, for a flat
+    slab (gradients along x), with their gradients: values (sigma_0, delta,
+    interface width, density ratio n_l/n_g), dW [4, groups] and dG [4].
+    ``make_lattice()`` returns a fresh lattice in the initial state (each
+    quantity runs its own forward and adjoint pass)."""
+    vals, dWs, dGs = [], [], []
+    runs = [lambda lat: sigma_and_gradient(lat, steps, checkpoint_every),
+            lambda lat: tolman_and_gradient(lat, steps, checkpoint_every),
+            lambda lat: density_functional_and_gradient(lat, steps, interface_width(n_liquid, n_gas),
+                                                        checkpoint_every),
+            lambda lat: density_functional_and_gradient(lat, steps, density_ratio(x_liquid, x_gas),
+                                                        checkpoint_every)]
+    for run in runs:
+        lat = make_lattice()
+        try:
+            v, dW, dG, _ = run(lat)
+        finally:
+            lat.close()
+        vals.append(v)
+        dWs.append(dW)
+        dGs.append(dG)
+    return np.array(vals), np.array(dWs), np.array(dGs)
+
+
+def tune_slab(make_lattice, weights_of, knobs, G, targets, steps, x_liquid, x_gas, n_liquid, n_gas,
+              checkpoint_every=100, rtol=1e-3, max_iter=10):
+    """Gradient solve replacing the hand tuning of Sec. V: Newton steps on the
+    stencil knobs and G until (sigma_0, delta, width, n_l/n_g) of a relaxed
+    flat slab match ``targets`` to ``rtol`` (relative).
+
+    ``weights_of(knobs)`` gives the group weights, linear in the knobs (the
+    paper's tables are); ``make_lattice(weights, G)`` a fresh lattice in the
+    initial state.  With as many knobs plus G as targets the Newton system is
+    square; otherwise it is solved in the least-squares sense.  Returns
+    (knobs, G, values, history of the relative errors)."""
+    knobs = np.array(knobs, dtype=np.float64)
+    targets = np.asarray(targets, dtype=np.float64)
+    base = np.asarray(weights_of(np.zeros_like(knobs)), dtype=np.float64)
+    slope = np.stack([np.asarray(weights_of(np.eye(len(knobs))[k]), dtype=np.float64) - base
+                      for k in range(len(knobs))], axis=1)          # dW/dknob
+    hist = []
+    vals = None
+    for _ in range(max_iter):
+        W = np.asarray(weights_of(knobs), dtype=np.float64)
+        vals, dW, dG = slab_observables(lambda: make_lattice(W, G), steps, x_liquid, x_gas,
+                                        n_liquid, n_gas, checkpoint_every)
+        rel = (vals - targets) / targets
+        hist.append(rel)
+        if np.max(np.abs(rel)) < rtol:
+            break
+        J = np.concatenate([dW @ slope, dG[:, None]], axis=1) / targets[:, None]
+        dx = np.linalg.lstsq(J, -rel, rcond=None)[0]
+        knobs = knobs + dx[:-1]
+        G = G + dx[-1]
+    return knobs, G, vals, hist
+
+
 _FN = None
 
 
@@ -303,4 +361,5 @@ def flat_sigma(W, G, spec):
 
 
 __all__ = ["Adjoint", "sigma_and_gradient", "density_functional_and_gradient", "density_ratio",
-           "interface_width", "tolman_and_gradient", "flat_sigma", "LbError"]
+           "interface_width", "tolman_and_gradient", "slab_observables", "tune_slab", "flat_sigma",
+           "LbError"]

@@ -272,3 +272,30 @@ def test_tolman_gradient_matches_oracle_finite_differences(case):
         fd = (_oracle_delta(lattice, shape, st.groups, tau, G, conv, gp, steps) -
               _oracle_delta(lattice, shape, st.groups, tau, G, conv, gm, steps)) / (2 * h)
         assert abs(lam[idx] - fd) < 1e-5 * abs(fd) + 1e-8, (idx, lam[idx], fd)
+
+
+def test_gradient_solve_of_sigma_and_tolman_at_fixed_profile():
+    """The tuning the paper does by hand (Sec. V) as a gradient solve: the
+    knobs sigma0_hat, sigma1_hat, delta0_hat of Table tab:e4e6e8_tuning_6 and
+    G move a relaxed slab to 1.1 x its sigma_0 and 0.5 x its Tolman length
+    while its interface width and density ratio stay where they were, all
+    four to 1e-3 relative."""
+    nx, ny, steps, K = 64, 4, 1500, 250
+    rho = L.tanh_slab(nx, ny, 1, 16, 48, N_GAS, N_LIQ, 2.0)
+    st0 = L.stencil_e4e6e8_tuning_6(2, 0, 0, 0)
+
+    def weights_of(k):
+        s0, s1, d0 = (Fr(float(v)).limit_denominator(10 ** 15) for v in k)
+        return L.stencil_e4e6e8_tuning_6(2, s0, s1, d0).weights
+
+    def make(W, G):
+        return P.Lattice("D2Q9", (nx, ny), rho, st0.bases, W, G=G)
+
+    knobs0, G0 = np.array([-0.1, 0.0, 0.05]), -3.0
+    v0, _, _ = AD.slab_observables(lambda: make(weights_of(knobs0), G0), steps, nx // 2, 0,
+                                   N_LIQ, N_GAS, K)
+    assert v0[0] > 0 and v0[3] > 1.0
+    targets = v0 * np.array([1.1, 0.5, 1.0, 1.0])
+    knobs, G, vals, hist = AD.tune_slab(make, weights_of, knobs0, G0, targets, steps, nx // 2, 0,
+                                        N_LIQ, N_GAS, K, rtol=1e-3, max_iter=10)
+    assert np.max(np.abs(vals / targets - 1.0)) < 1e-3, (knobs, G, vals, targets, hist)
