@@ -52,17 +52,20 @@ struct Tile {
     int inst, x0, y0, y1;
 };
 
-__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+// Halo gather: lane l pulls population SLOT_POP[l >> 2] of halo column l & 3.
+// Xor-shuffles over 4, 8 and 16 lanes then add the slots in pairs (1,3),
+// (2,4), (5,7), (6,8), their pairs and the two halves -- dens9's tree, so the
+// halo density equals the one the owning strip forms, bit for bit.
+constexpr int SLOT_POP[8] = {1, 3, 2, 4, 5, 7, 6, 8};
 
-// pulled populations of node (x, y): g_i = A_i(x - xi_i), periodic
-__device__ __forceinline__ void pull9(const float *__restrict__ A, int N, int nx, int ny, int x,
-                                      int y, float *g) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int sx = wrap1(x - cvel<9>(i, 0), nx), sy = wrap1(y - cvel<9>(i, 1), ny);
-        g[i] = __ldg(A + (long long)i * N + (long long)sy * nx + sx);
-    }
+__host__ __device__ constexpr unsigned slot_pack(int mu) {   // mu < 0: the population
+    unsigned v = 0;
+    for (int s = 0; s < 8; ++s)
+        v |= mu < 0 ? (unsigned)SLOT_POP[s] << (4 * s)
+                    : (unsigned)(cvel<9>(SLOT_POP[s], mu) + 1) << (2 * s);
+    return v;
 }
+constexpr unsigned SLOT_P = slot_pack(-1), SLOT_X = slot_pack(0), SLOT_Y = slot_pack(1);
 
 // shifted density: opposite pairs first (1,3), (2,4), (5,7), (6,8)
 __device__ __forceinline__ float dens9(const float *g) {
@@ -108,18 +111,21 @@ __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, flo
 // One warp marches rows y0 - 2 .. y1 + 1 of the 32-column strip [x0, x0 + 32)
 // of lattice I and collides rows y0 .. y1 - 1.  Per row r: the lanes pull the
 // row's populations f_i(x, r) = A_i(x - xi_i, r - xi_iy) (coalesced rows),
-// form n and psi of their node (lanes 0..3 also of the halo columns x0 - 2,
-// x0 - 1, x0 + 32, x0 + 33) into the warp's row buffer, and add row r's share
-// of the force to the five target rows r - 2 .. r + 2 it touches: with
-// in-row sums X1 = psi(x+1) - psi(x-1), X2 = psi(x+2) - psi(x-2) and S1, S2
-// the pair sums relative to psi(x),
+// form n and psi of their node, gather n of the halo columns x0 - 2, x0 - 1,
+// x0 + 32, x0 + 33 (one load per lane, see SLOT_POP), put psi into the
+// warp's row buffer, and add row r's share of the force to the five target
+// rows r - 2 .. r + 2 it touches: with in-row sums X1 = psi(x+1) - psi(x-1),
+// X2 = psi(x+2) - psi(x-2) and S1, S2 the pair sums relative to psi(x),
 //   F_x(t) += W(1+d^2) X1 + 2 W(4+d^2) X2,  F_y(t) += d (W(1+d^2) S1 + W(4+d^2) S2)
 // for d = r - t, plus (once per target) sum_d d M_d (psi(x, t+d) - psi(x, t-d))
 // with M_d = sum over the row of W(dx^2 + d^2) -- the exact form of eq. sc_f
 // for the 2D groups up to (2,2).  Row r - 2 is then complete: it is collided
 // from the populations the lane has held since it pulled them, and written.
-// Sizes that are not multiples of 32: lanes past the edge work on the
-// periodic image and store nothing.
+// Periodic wrap: the source columns of a lane are fixed for the march and
+// the three source rows advance by one row offset per row, so no load
+// computes a wrap.  Sizes that are not multiples of 32: lanes past the edge
+// work on the periodic image and store nothing.  Offsets are 32-bit
+// (9 nx ny < 2^31, checked when the path is chosen).
 __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int parity,
                                       float *row, int lane) {
     const int nx = I.nx, ny = I.ny, N = nx * ny;
@@ -129,9 +135,30 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
     const int gx = x0 + lane;
     const bool xown = gx < nx;
     const int x = gx % nx;
-    int hx = (lane < 2 ? x0 - 2 + lane : x0 + 30 + lane) % nx;
-    hx += hx < 0 ? nx : 0;
-    const int hpos = lane < 2 ? lane : lane + 32;
+    int cs[3];                         // source column x - c for c = -1, 0, 1
+    cs[0] = x + 1 == nx ? 0 : x + 1;
+    cs[1] = x;
+    cs[2] = x == 0 ? nx - 1 : x - 1;
+    // the lane's halo load: population hp of column hc
+    const int slot = lane >> 2, hcol = lane & 3;
+    int hc = (hcol < 2 ? x0 - 2 + hcol : x0 + 30 + hcol) % nx;
+    hc += hc < 0 ? nx : 0;
+    const int hp = (int)((SLOT_P >> (4 * slot)) & 15u);
+    const int hcx = (int)((SLOT_X >> (2 * slot)) & 3u) - 1, hcy = (int)((SLOT_Y >> (2 * slot)) & 3u) - 1;
+    int hs = hc - hcx;
+    hs += hs < 0 ? nx : 0;
+    hs -= hs >= nx ? nx : 0;
+    const int hoff = hp * N + hs;
+    const int hpos = lane < 2 ? lane : lane + 32;   // lanes 0..3: columns x0-2, x0-1, x0+32, x0+33
+    // offsets of the source rows r + 1, r, r - 1 of the row being pulled
+    int rr[3];
+    {
+        int r = y0 - 2;
+        r += r < 0 ? ny : 0;
+        rr[1] = r * nx;
+        rr[0] = (r + 1 == ny ? 0 : r + 1) * nx;
+        rr[2] = (r == 0 ? ny - 1 : r - 1) * nx;
+    }
     float gq[3][9], dq[3];
     float ps[5], ax[5], ay[5];
 #pragma unroll
@@ -139,31 +166,36 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
     bool bad = false;
     const int nit = (y1 - y0) + 4;
     // the next row's populations are in flight while this row is computed
-    float gn[9], ghn[9];
-    auto row_of = [&](int it) {
-        int yr = (y0 - 2 + it) % ny;
-        return yr + (yr < 0 ? ny : 0);
-    };
-    pull9(A, N, nx, ny, x, row_of(0), gn);
-    if (lane < 4) pull9(A, N, nx, ny, hx, row_of(0), ghn);
-    for (int it = 0; it < nit; ++it) {
-        float gh[9];
+    float gn[9], hn = 0.f, hn0 = 0.f;
+    auto pull = [&]() {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            gq[2][i] = gn[i];
-            gh[i] = ghn[i];
-        }
+        for (int i = 0; i < 9; ++i)
+            gn[i] = __ldg(A + (i * N + rr[cvel<9>(i, 1) + 1] + cs[cvel<9>(i, 0) + 1]));
+        hn = __ldg(A + (hoff + (hcy == 0 ? rr[1] : (hcy < 0 ? rr[0] : rr[2]))));
+        if (lane < 4) hn0 = __ldg(A + (rr[1] + hc));
+    };
+    pull();
+    int ot = y0 * nx;                  // offset of the next row to be written
+    for (int it = 0; it < nit; ++it) {
+        const float h1 = hn, h0 = hn0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gq[2][i] = gn[i];
         if (it + 1 < nit) {
-            const int yn = row_of(it + 1);
-            pull9(A, N, nx, ny, x, yn, gn);
-            if (lane < 4) pull9(A, N, nx, ny, hx, yn, ghn);
+            rr[2] = rr[1];
+            rr[1] = rr[0];
+            rr[0] += nx;
+            rr[0] = rr[0] == N ? 0 : rr[0];
+            pull();
         }
         dq[2] = dens9(gq[2]);
         const float n = dq[2] + I.rho0;
         bad |= xown && it >= 2 && it < nit - 2 && !(n > 0.f);
         ps[4] = fc::psi32(n);
+        float hsum = h1 + __shfl_xor_sync(0xffffffffu, h1, 4);
+        hsum += __shfl_xor_sync(0xffffffffu, hsum, 8);
+        hsum += __shfl_xor_sync(0xffffffffu, hsum, 16);
         float psh = 0.f;
-        if (lane < 4) psh = fc::psi32(dens9(gh) + I.rho0);
+        if (lane < 4) psh = fc::psi32((h0 + hsum) + I.rho0);
         __syncwarp();   // the previous row's readers are done
         row[lane + 2] = ps[4];
         if (lane < 4) row[hpos] = psh;
@@ -187,17 +219,17 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
         ax[4] += cx2;
         ay[4] -= cz2;
         if (it >= 4) {   // row t = y0 - 4 + it is complete
-            const int t = y0 - 4 + it;
             float fy = fmaf(I.M1, ps[3] - ps[1], ay[0]);
             fy = fmaf(I.M2, ps[4] - ps[0], fy);
             const float pre = I.mGp * ps[2];
             float out[9];
             collide9(gq[0], dq[0], pre * ax[0], pre * fy, I, out);
             if (xown) {
-                const long long s = (long long)t * nx + x;
+                float *dst = B + (ot + x);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) B[(long long)i * N + s] = out[i];
+                for (int i = 0; i < 9; ++i) __stwb(dst + i * N, out[i]);
             }
+            ot += nx;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
