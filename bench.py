@@ -56,10 +56,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# the sources that decide what the fused D3Q19 step kernel reads and writes:
+# the kernel, its helpers and parameters, and the padded population layout
+# (api.cu); the 2D, binary64 and adjoint units do not enter
+FUSED_SOURCES = ("api.cu", "expcr.cuh", "fused3d.cu", "fused3d_tma.cu", "fusedcommon.cuh",
+                 "internal.h", "kernels.cuh")
+
+
 def _src_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_23647_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in FUSED_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -277,14 +277,16 @@ __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d(const Inst I, int rows,
 }
 
 // many lattices: a resident grid of warps walks the table of (lattice,
-// strip, row chunk) items; the last block advances every lattice's counter
+// strip, row chunk) items, dealt round-robin over the blocks first (item k
+// to block k mod grid) so that a table shorter than the grid's warps still
+// spreads over every block; the last block advances every lattice's counter
 __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d_batch(const Inst *__restrict__ insts,
                                                             const Tile *__restrict__ items,
                                                             int nitems, int ninst, int parity,
                                                             unsigned long long *done) {
     __shared__ float buf[WPB][32 + 2 * R];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int k = blockIdx.x * WPB + w; k < nitems; k += gridDim.x * WPB) {
+    for (int k = w * gridDim.x + blockIdx.x; k < nitems; k += gridDim.x * WPB) {
         const Tile it = items[k];
         march(insts[it.inst], it.x0, it.y0, it.y1, parity, buf[w], lane);
     }
