@@ -85,7 +85,10 @@ def critical_coupling(e2=1.0, psi=psi_exp, dpsi=dpsi_exp, n0=1.0):
 
 def coexistence(Gp, eps=0.0, e2=1.0, psi=psi_exp, dpsi=dpsi_exp, guess=(0.2, 2.0)):
     """(n_g, n_l, p0) from eq. ``SCMaxwell``: equal pressure and a vanishing
-    integral with measure dn psi'/psi^(eps+1)."""
+    integral with measure dn psi'/psi^(eps+1).  Raises RuntimeError when the
+    root finder stops short of a root (residuals above 1e-12) or falls onto
+    the single-phase root n_g = n_l: the guess must lie in the basin of the
+    two-phase root."""
     def P(n):
         return bulk_pressure(n, Gp, e2, psi)
 
@@ -98,7 +101,12 @@ def coexistence(Gp, eps=0.0, e2=1.0, psi=psi_exp, dpsi=dpsi_exp, guess=(0.2, 2.0
         p0 = P(ng)
         return [P(nl) - p0, integral(ng, nl, p0)]
     ng, nl = optimize.fsolve(eqs, list(guess), xtol=1e-13)
-    return float(ng), float(nl), float(P(ng))
+    r = eqs([ng, nl])
+    p0 = P(ng)
+    if not (abs(r[0]) <= 1e-12 * max(1.0, abs(p0)) and abs(r[1]) <= 1e-12 and nl - ng > 1e-6):
+        raise RuntimeError(f"coexistence: no two-phase root from guess {tuple(guess)} "
+                           f"(n_g {ng:.6g}, n_l {nl:.6g}, residuals {r[0]:.2e}, {r[1]:.2e})")
+    return float(ng), float(nl), float(p0)
 
 
 def _profile_slope2(n, ng, p0, Gp, eps, e2, psi, dpsi):

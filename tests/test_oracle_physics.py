@@ -316,3 +316,26 @@ def test_critical_coupling_of_exp_pseudopotential():
     Gpc, nc = A.critical_coupling()
     assert abs(3.0 * Gpc - G.scalars()["Gc_paper_exp"][0]) < 1e-6
     assert abs(nc - 1.0) < 1e-5
+
+
+def test_coexistence_refuses_a_non_root():
+    """eq. SCMaxwell has a two-phase root and the trivial n_g = n_l; a guess
+    outside the two-phase basin must raise, not come back as the answer.
+    psi_eps with eps = 14/29 at 1.1 G'_c: from (0.5, 2.0) the solver stalls;
+    from (0.4, 1.4) it reaches the root, where the pressures are equal and
+    the weighted area of eq. SCMaxwell vanishes."""
+    eps = 14.0 / 29.0
+    f, df = A.psi_eps_fn(eps)
+    Gc, nc = A.critical_coupling(psi=f, dpsi=df)
+    Gp = 1.1 * Gc
+    with pytest.raises(RuntimeError):
+        A.coexistence(Gp, eps, psi=f, dpsi=df, guess=(0.5, 2.0))
+    ng, nl, p0 = A.coexistence(Gp, eps, psi=f, dpsi=df, guess=(0.4, 1.4))
+    assert ng < nc < nl
+    P = lambda n: A.bulk_pressure(n, Gp, 1.0, f)
+    assert abs(P(ng) - p0) < 1e-15 and abs(P(nl) - p0) < 1e-14
+    # the area rule with the trapezoid rule on a fine grid
+    m = np.linspace(ng, nl, 200001)
+    integrand = df(m) / f(m) ** (eps + 1.0) * (p0 - P(m))
+    area = np.sum(0.5 * (integrand[1:] + integrand[:-1]) * np.diff(m))
+    assert abs(area) < 1e-9
