@@ -311,6 +311,71 @@ def run_gb300(args, dist, rank, ws):
         lit = {"value": N * 60 / (msl * 1e3), "unit": "MLUPS", "steps": 60, "warmup": 3,
                "stable": okl}
 
+    # the same bubble with psi_eps (eq. psieps; eps = 10/31 of the E8 stencil's
+    # e4 by eq. eps_moments) at 1.1 times its critical coupling, started from
+    # its coexistence pair: the fused kernel's psi_eps instantiation
+    peps = None
+    if not args.no_psi_eps:
+        pe = L.PSI_EPS_BUBBLE
+        rho_e = L.tanh_sphere(NX, NY, NZ, RADIUS, pe["n_gas"], pe["n_liquid"], 2.0)
+        late = P.Lattice("D3Q19", (NX, NY, NZ), rho_e, L.E8_3D.bases, L.E8_3D.weights,
+                         precision="fp32", tau=1.0, G=pe["Gp"], convention="literal",
+                         psi_eps=pe["eps"], stream=stream.cuda_stream)
+        fused_e = P.lb_fused_active(late.ctx)
+        late.step(args.warmup)
+        ke = min(args.steps, 1000)
+        P.lb_timing(late.ctx, 1)
+        e0.record(stream)
+        late.step(ke)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = e0.elapsed_time(e1)
+        kte = P.lb_timing_read(late.ctx)
+        P.lb_timing(late.ctx, 0)
+        oke = late.sync() == P.LB_OK
+        obe = late.observables()
+        late.close()
+        kfe = kte.get("fused", (0.0, 0))
+        ve = N * ke / (mse * 1e3)
+        peps = {"value": ve, "unit": "MLUPS", "steps": ke, "ms_per_step": mse / ke,
+                "eps": pe["eps"], "Gp": pe["Gp"], "densities": [pe["n_gas"], pe["n_liquid"]],
+                "fused_kernel": fused_e,
+                "kernel_ms_avg": kfe[0] / kfe[1] if kfe[1] else None,
+                "hbm_frac": ALG_BYTES["fused"] * N / (kfe[0] / kfe[1] * 1e-3) / 1e9 / peak
+                if kfe[1] else None,
+                "stable": oke, "rho_min": obe["rho_min"], "rho_max": obe["rho_max"]}
+
+    # the same bubble with the F^2 forcing variant (Sec. VI: T = 2 u F -
+    # (A/tau) F F in eq. GuoForcing; the paper fixes no A, this uses 0.25):
+    # the fused kernel's F^2 instantiation
+    f2 = None
+    if not args.no_f2:
+        A_f2 = 0.25
+        latf = P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), L.E8_3D.bases,
+                         L.E8_3D.weights, precision="fp32", tau=1.0, G=G, convention=CONVENTION,
+                         forcing_A=A_f2, stream=stream.cuda_stream)
+        fused_f = P.lb_fused_active(latf.ctx)
+        latf.step(args.warmup)
+        kf = min(args.steps, 1000)
+        P.lb_timing(latf.ctx, 1)
+        e0.record(stream)
+        latf.step(kf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msf = e0.elapsed_time(e1)
+        ktf = P.lb_timing_read(latf.ctx)
+        P.lb_timing(latf.ctx, 0)
+        okf = latf.sync() == P.LB_OK
+        latf.close()
+        kff = ktf.get("fused", (0.0, 0))
+        vf = N * kf / (msf * 1e3)
+        f2 = {"value": vf, "unit": "MLUPS", "steps": kf, "ms_per_step": msf / kf, "A": A_f2,
+              "fused_kernel": fused_f,
+              "kernel_ms_avg": kff[0] / kff[1] if kff[1] else None,
+              "hbm_frac": ALG_BYTES["fused"] * N / (kff[0] / kff[1] * 1e-3) / 1e9 / peak
+              if kff[1] else None,
+              "stable": okf}
+
     # FP64 path on the same workload (fewer steps; binary64 arithmetic)
     fp64 = None
     if not args.no_fp64:
@@ -437,7 +502,9 @@ def run_gb300(args, dist, rank, ws):
                        "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (2 x 1.27 GB populations)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "fp64": fp64, "literal_g": lit, "fused_kernel": fused,
+            "gpu_launches": launches, "fp64": fp64, "literal_g": lit, "psi_eps": peps,
+            "f2_forcing": f2,
+            "fused_kernel": fused,
             "batched_2d": batched, "adjoint": adjoint,
             "observables": {"mass": obs["mass"], "umax": obs["umax"],
                             "rho_min": obs["rho_min"], "rho_max": obs["rho_max"],
@@ -456,6 +523,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-literal", action="store_true")
+    ap.add_argument("--no-psi-eps", action="store_true")
+    ap.add_argument("--no-f2", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--zchunk", type=int, default=0,

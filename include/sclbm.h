@@ -74,8 +74,10 @@ enum { LB_G_LITERAL = 0, LB_G_TIMES_CS2 = 1 };
 /* Pseudopotential: LB_PSI_EXP psi = exp(-1/n) (Sec. IV B); LB_PSI_EPS
  * psi_eps = (n/(eps+n))^(1/eps) (eq. psieps, Sec. IV B / V C, e.g.
  * eps = 14/29 with e4 = 4/5), evaluated in binary64 as
- * RN(RN(n/RN(eps+n))^RN(1/eps)) with a correctly rounded power.  The fused
- * kernels and batches serve LB_PSI_EXP; LB_PSI_EPS runs the two-kernel path. */
+ * RN(RN(n/RN(eps+n))^RN(1/eps)) with a correctly rounded power.  The
+ * shifted-binary32 paths (two-kernel, fused D3Q19 and D2Q9, batches) all form
+ * psi_eps as powf(n / (eps + n), 1/eps) in binary32, so every FP32 path uses
+ * the same psi; a batch may mix both kinds. */
 enum { LB_PSI_EXP = 0, LB_PSI_EPS = 1 };
 
 /* Largest number of (e,-e) pairs and largest |component| of a stencil vector. */
@@ -94,7 +96,7 @@ typedef struct lb_params {
     double rho0_shift;  /* rho0 of the FP32 shift g_i = f_i - w_i rho0 (default 0.5) */
     double forcing_A;   /* F^2 forcing variant: the tensor of eq. GuoForcing is
                            T = 2 u F - (A/tau) F F (Sec. VI); 0 (default) is
-                           Guo's T = 2 u F.  Nonzero A runs the two-kernel path. */
+                           Guo's T = 2 u F.  Every path serves nonzero A. */
 } lb_params;
 
 typedef struct lb_stencil_info {
@@ -268,8 +270,11 @@ lb_status lb_timing_read(lb_ctx *ctx, double *ms, long long *launches);
  *
  * Members are contexts created by lb_create: D2Q9, LB_FP32_SHIFTED, stencil
  * set, every group among (1,0), (1,1), (2,0), (2,1), (2,2) (E4, E6, E8 and
- * their tuned variants); LB_EUNSUPPORTED otherwise, LB_ESTATE if a stencil
- * is missing, LB_EINVAL for a repeated or NULL member.  The batch borrows
+ * their tuned variants), either pseudopotential and either forcing variant
+ * (a batch whose members differ in these runs a kernel that picks per
+ * member, slower than the one a uniform batch runs); LB_EUNSUPPORTED
+ * otherwise, LB_ESTATE if a stencil is missing, LB_EINVAL for a repeated or
+ * NULL member.  The batch borrows
  * the members (their buffers, counters and host step counts advance with
  * lb_batch_step); destroy the batch before any member.  A member may still
  * be used on its own between batch calls: lb_batch_step orders itself after

@@ -174,6 +174,16 @@ def named_stencil(name):
 
 
 # --- density fields -----------------------------------------------------------
+# psi_eps workload of the benchmark (D3Q19 E8 bubble): eps = 10/31 is the eps
+# that eq. eps_moments gives for the E8 stencils' e4 = 4/7 (e2 = 1);
+# Gp = 1.1 G'_c of psi_eps at that eps (literal reading); n_gas, n_liquid its
+# coexistence pair from eq. SCMaxwell.  tests/test_oracle_physics.py checks
+# the three numbers against the oracle's critical point and Maxwell
+# construction.
+PSI_EPS_BUBBLE = {"eps": 10.0 / 31.0, "Gp": -2.6857441579840247,
+                  "n_gas": 0.43663686360362103, "n_liquid": 1.5757138898336904}
+
+
 def _coords(nx, ny, nz):
     z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64),
                           np.arange(ny, dtype=np.float64),

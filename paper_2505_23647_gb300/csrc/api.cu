@@ -199,6 +199,7 @@ void set_consts(lb_ctx *c) {
     c->k.psi_kind = c->p.psi_kind;
     c->k.psi_eps = c->p.psi_kind == LB_PSI_EPS ? c->p.psi_eps : 0.0;
     c->k.psi_inv = c->p.psi_kind == LB_PSI_EPS ? 1.0 / c->p.psi_eps : 0.0;
+    fill_mass_exact_f32(c->k, c->Q);
 }
 
 size_t tsize(const lb_ctx *c) { return c->p.precision == LB_FP64 ? 8 : 4; }

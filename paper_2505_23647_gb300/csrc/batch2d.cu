@@ -9,8 +9,8 @@
 // a row is collided and written as soon as the two rows above it are known.
 // Warps synchronise only with themselves, so there is no block-wide barrier
 // in the step.  Forcing stencils are any weights on the 2D groups (1,0),
-// (1,1), (2,0), (2,1), (2,2) (E4, E6, E8 and their tuned variants), per
-// lattice.
+// (1,1), (2,0), (2,1), (2,2) (E4, E6, E8 and their tuned variants), and the
+// pseudopotential is exp(-1/n) or psi_eps (eq. psieps), both per lattice.
 //
 // Batches (lb_batch_*): the (lattice, strip, row chunk) items of all lattices
 // form one table walked by a grid of resident warps, so boxes of uneven size
@@ -45,6 +45,10 @@ struct Inst {
     // 3 omega w, 9 cw, 3 cw
     float omw[3], m3cw[3], b45[3], d3[3], c9[3], c3[3];
     float M1, M2;       // row sums of the weights at |d| = 1, 2 (M2 doubled)
+    float eps, inv_eps; // psi_eps: eps and RN(1/eps) (0 for psi = exp(-1/n))
+    // F^2 variant (T = 2 u F - (A/tau) F F): -kA/2 and, per class, -4.5 cw kA
+    // (kA = A/tau; all 0 for Guo's T = 2 u F)
+    float mhkA, kq[3];
 };
 
 // one work item of a batch: rows [y0, y1) of the strip [x0, x0 + 32) of lattice inst
@@ -76,6 +80,9 @@ __device__ __forceinline__ float dens9(const float *g) {
 // fc::collide19: for a pair (xi, -xi) of class weight w,
 //   E = omega w (base + 4.5 n (xi.u)^2) + cw (9 (xi.u)(xi.F) - 3 u.F)
 //   O = 3 omega w n (xi.u) + 3 cw (xi.F),  out(+-xi) = (1 - omega) g(+-xi) + E +- O.
+// F2: the F^2 variant's extra source -cw kA (4.5 (xi.F)^2 - 1.5 F.F) (Sec. VI),
+// its F.F part folded into u.F and its (xi.F)^2 part added to E.
+template <bool F2>
 __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, float Fy,
                                          const Inst &I, float *out) {
     const float n = dn + I.rho0;
@@ -86,7 +93,8 @@ __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, flo
     const float ux = fmaf(0.5f, Fx, jx) * inv;
     const float uy = fmaf(0.5f, Fy, jy) * inv;
     const float uu = fmaf(ux, ux, uy * uy);
-    const float uF = fmaf(ux, Fx, uy * Fy);
+    float uF = fmaf(ux, Fx, uy * Fy);
+    if constexpr (F2) uF = fmaf(I.mhkA, fmaf(Fx, Fx, Fy * Fy), uF);
     const float base = fmaf(-1.5f * n, uu, dn);
     out[0] = fmaf(I.keep, g[0], fmaf(I.omw[0], base, I.m3cw[0] * uF));
     const float a1 = fmaf(I.omw[1], base, I.m3cw[1] * uF);
@@ -96,7 +104,9 @@ __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, flo
 #define SCLBM_PAIR9(P, M, C, CU, CF)                                            \
     {                                                                           \
         const float cu = (CU), cF = (CF);                                       \
-        const float ev = fmaf(cu, fmaf(b##C, cu, I.c9[C] * cF), a##C);          \
+        float aq = a##C;                                                        \
+        if constexpr (F2) aq = fmaf(cF, I.kq[C] * cF, aq);                      \
+        const float ev = fmaf(cu, fmaf(b##C, cu, I.c9[C] * cF), aq);            \
         const float od = fmaf(e##C, cu, I.c3[C] * cF);                          \
         out[P] = fmaf(I.keep, g[P], ev + od);                                   \
         out[M] = fmaf(I.keep, g[M], ev - od);                                   \
@@ -126,6 +136,7 @@ __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, flo
 // computes a wrap.  Sizes that are not multiples of 32: lanes past the edge
 // work on the periodic image and store nothing.  Offsets are 32-bit
 // (9 nx ny < 2^31, checked when the path is chosen).
+template <bool EPS, bool F2>
 __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int parity,
                                       float *row, int lane) {
     const int nx = I.nx, ny = I.ny, N = nx * ny;
@@ -190,12 +201,12 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
         dq[2] = dens9(gq[2]);
         const float n = dq[2] + I.rho0;
         bad |= xown && it >= 2 && it < nit - 2 && !(n > 0.f);
-        ps[4] = fc::psi32(n);
+        ps[4] = fc::psi_fused<EPS>(n, I.eps, I.inv_eps);
         float hsum = h1 + __shfl_xor_sync(0xffffffffu, h1, 4);
         hsum += __shfl_xor_sync(0xffffffffu, hsum, 8);
         hsum += __shfl_xor_sync(0xffffffffu, hsum, 16);
         float psh = 0.f;
-        if (lane < 4) psh = fc::psi32((h0 + hsum) + I.rho0);
+        if (lane < 4) psh = fc::psi_fused<EPS>((h0 + hsum) + I.rho0, I.eps, I.inv_eps);
         __syncwarp();   // the previous row's readers are done
         row[lane + 2] = ps[4];
         if (lane < 4) row[hpos] = psh;
@@ -223,7 +234,7 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
             fy = fmaf(I.M2, ps[4] - ps[0], fy);
             const float pre = I.mGp * ps[2];
             float out[9];
-            collide9(gq[0], dq[0], pre * ax[0], pre * fy, I, out);
+            collide9<F2>(gq[0], dq[0], pre * ax[0], pre * fy, I, out);
             if (xown) {
                 float *dst = B + (ot + x);
 #pragma unroll
@@ -254,10 +265,34 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
     }
 }
 
+// march modes: bit 0 psi_eps, bit 1 the F^2 forcing variant; MIXED picks
+// per lattice (a batch whose lattices differ in either)
+constexpr int MIXED = 4;
+
+__host__ __device__ inline int inst_mode(const Inst &I) {
+    return (I.inv_eps != 0.f ? 1 : 0) | (I.mhkA != 0.f ? 2 : 0);
+}
+
+template <int MODE>
+__device__ __forceinline__ void march_mode(const Inst &I, int x0, int y0, int y1, int parity,
+                                           float *row, int lane) {
+    if constexpr (MODE != MIXED) {
+        march<(MODE & 1) != 0, (MODE & 2) != 0>(I, x0, y0, y1, parity, row, lane);
+    } else {
+        switch (inst_mode(I)) {
+            case 0: march<false, false>(I, x0, y0, y1, parity, row, lane); break;
+            case 1: march<true, false>(I, x0, y0, y1, parity, row, lane); break;
+            case 2: march<false, true>(I, x0, y0, y1, parity, row, lane); break;
+            default: march<true, true>(I, x0, y0, y1, parity, row, lane); break;
+        }
+    }
+}
+
 constexpr int WPB = 8;   // warps (strips) per block
 
 // one lattice: warp k of the grid marches strip k % nstrips, row chunk
 // k / nstrips; the last block advances the step counter
+template <int MODE>
 __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d(const Inst I, int rows, int parity) {
     __shared__ float buf[WPB][32 + 2 * R];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -265,7 +300,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d(const Inst I, int rows,
     const int k = blockIdx.x * WPB + w;
     const int y0 = (k / nstrips) * rows;
     if (y0 < I.ny)
-        march(I, (k % nstrips) * 32, y0, min(y0 + rows, I.ny), parity, buf[w], lane);
+        march_mode<MODE>(I, (k % nstrips) * 32, y0, min(y0 + rows, I.ny), parity, buf[w], lane);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -280,6 +315,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d(const Inst I, int rows,
 // strip, row chunk) items, dealt round-robin over the blocks first (item k
 // to block k mod grid) so that a table shorter than the grid's warps still
 // spreads over every block; the last block advances every lattice's counter
+template <int MODE>
 __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d_batch(const Inst *__restrict__ insts,
                                                             const Tile *__restrict__ items,
                                                             int nitems, int ninst, int parity,
@@ -288,7 +324,7 @@ __global__ void __launch_bounds__(WPB * 32, 2) k_strip2d_batch(const Inst *__res
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = w * gridDim.x + blockIdx.x; k < nitems; k += gridDim.x * WPB) {
         const Tile it = items[k];
-        march(insts[it.inst], it.x0, it.y0, it.y1, parity, buf[w], lane);
+        march_mode<MODE>(insts[it.inst], it.x0, it.y0, it.y1, parity, buf[w], lane);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -310,20 +346,38 @@ constexpr int ROWS_ONE = 16;   // row chunk of a single lattice
 
 void launch_one(const Inst &I, int parity, cudaStream_t st) {
     const int items = ((I.nx + 31) / 32) * ((I.ny + ROWS_ONE - 1) / ROWS_ONE);
-    k_strip2d<<<(items + WPB - 1) / WPB, WPB * 32, 0, st>>>(I, ROWS_ONE, parity);
+    const int g = (items + WPB - 1) / WPB;
+    switch (inst_mode(I)) {
+        case 0: k_strip2d<0><<<g, WPB * 32, 0, st>>>(I, ROWS_ONE, parity); break;
+        case 1: k_strip2d<1><<<g, WPB * 32, 0, st>>>(I, ROWS_ONE, parity); break;
+        case 2: k_strip2d<2><<<g, WPB * 32, 0, st>>>(I, ROWS_ONE, parity); break;
+        default: k_strip2d<3><<<g, WPB * 32, 0, st>>>(I, ROWS_ONE, parity); break;
+    }
 }
 
-void launch_batch_shape(int, const Inst *insts, const Tile *items, int nitems, int ninst,
+// the batch kernel of a mode (0..3: every lattice alike, MIXED)
+using BatchKernel = void (*)(const Inst *, const Tile *, int, int, int, unsigned long long *);
+inline BatchKernel batch_kernel(int mode) {
+    switch (mode) {
+        case 0: return k_strip2d_batch<0>;
+        case 1: return k_strip2d_batch<1>;
+        case 2: return k_strip2d_batch<2>;
+        case 3: return k_strip2d_batch<3>;
+        default: return k_strip2d_batch<MIXED>;
+    }
+}
+
+void launch_batch_shape(int mode, const Inst *insts, const Tile *items, int nitems, int ninst,
                         int parity, unsigned long long *done, int grid, cudaStream_t st) {
-    k_strip2d_batch<<<grid, WPB * 32, 0, st>>>(insts, items, nitems, ninst, parity, done);
+    batch_kernel(mode)<<<grid, WPB * 32, 0, st>>>(insts, items, nitems, ninst, parity, done);
 }
 
-// blocks of the batch kernel resident on the whole GPU
-int resident_grid(int) {
+// blocks of the batch kernel of a mode resident on the whole GPU
+int resident_grid(int mode) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_strip2d_batch, WPB * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel(mode), WPB * 32, 0) !=
             cudaSuccess || per < 1)
         per = 1;
     return (sms > 0 ? sms : 1) * per;
@@ -334,8 +388,7 @@ int resident_grid(int) {
 // The 2D fused path applies to a shifted-binary32 D2Q9 context whose
 // stencil uses only the five 2D groups up to (2,2).
 bool fused2d_applicable(const lb_ctx *c, float *W5) {
-    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 9 || c->p.psi_kind != LB_PSI_EXP ||
-        c->p.forcing_A != 0.0)
+    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 9)
         return false;
     if (c->g.nx < 4 || c->g.ny < 4) return false;
     if ((long long)9 * c->g.N >= (1LL << 31)) return false;
@@ -372,12 +425,17 @@ static void inst_from_ctx(const lb_ctx *c, b2::Inst *I) {
     const double om = c->k.omega;
     I->mGp = (float)c->k.mGp;
     I->rho0 = (float)c->k.rho0;
-    I->keep = (float)(1.0 - om);
+    I->eps = c->k.psi_kind == LB_PSI_EPS ? (float)c->k.psi_eps : 0.f;
+    I->inv_eps = c->k.psi_kind == LB_PSI_EPS ? (float)c->k.psi_inv : 0.f;
+    I->keep = c->k.keep32;
     const double pref = 1.0 - 1.0 / (2.0 * c->p.tau);
     const double wc[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+    const double kA = c->k.kA;
+    I->mhkA = (float)(-0.5 * kA);
     for (int k = 0; k < 3; ++k) {
         const double cw = pref * wc[k];
-        I->omw[k] = (float)(om * wc[k]);
+        I->kq[k] = (float)(-4.5 * cw * kA);
+        I->omw[k] = c->k.omw32[k];   // mass-exact with keep
         I->m3cw[k] = (float)(-3.0 * cw);
         I->b45[k] = (float)(4.5 * om * wc[k]);
         I->d3[k] = (float)(3.0 * om * wc[k]);
@@ -412,6 +470,7 @@ struct lb_batch {
     int ntiles[b2::NSHAPE] = {};
     int grid[b2::NSHAPE] = {};
     int shape = 0;
+    int mode = 0;                      // march mode of the batch kernel (b2::MIXED: per lattice)
     unsigned long long *d_done = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -448,7 +507,7 @@ lb_status ensure_tiles(lb_batch *b, int s) {
     e = cudaMemcpy(b->d_tiles[s], t.data(), t.size() * sizeof(b2::Tile), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bfail(e, "lb_batch tile table");
     b->ntiles[s] = (int)t.size();
-    const int g = b2::resident_grid(s), need = (b->ntiles[s] + b2::WPB - 1) / b2::WPB;
+    const int g = b2::resident_grid(b->mode), need = (b->ntiles[s] + b2::WPB - 1) / b2::WPB;
     b->grid[s] = g < need ? g : need;
     return LB_OK;
 }
@@ -473,7 +532,7 @@ lb_status sync_inst(lb_batch *b) {
 
 void launch_steps(lb_batch *b, int s, int n) {
     for (int k = 0; k < n; ++k)
-        b2::launch_batch_shape(s, b->d_inst, b->d_tiles[s], b->ntiles[s], (int)b->ctx.size(), k & 1,
+        b2::launch_batch_shape(b->mode, b->d_inst, b->d_tiles[s], b->ntiles[s], (int)b->ctx.size(), k & 1,
                                b->d_done, b->grid[s], b->stream);
 }
 
@@ -546,6 +605,9 @@ lb_status lb_batch_create(lb_ctx *const *ctxs, int n, void *cuda_stream, lb_batc
     b->ctx.assign(ctxs, ctxs + n);
     b->inst.resize(n);
     for (int i = 0; i < n; ++i) inst_from_ctx(ctxs[i], &b->inst[i]);
+    b->mode = b2::inst_mode(b->inst[0]);
+    for (int i = 1; i < n; ++i)
+        if (b2::inst_mode(b->inst[i]) != b->mode) b->mode = b2::MIXED;
     cudaError_t e = cudaSuccess;
     if (cuda_stream) {
         b->stream = (cudaStream_t)cuda_stream;

@@ -10,7 +10,7 @@
 //   * the pulled populations A_i(x - xi_i) of the next plane (tile plus a
 //     radius-R halo) are copied into a double-buffered shared-memory stage
 //     with cp.async while the current plane is processed;
-//   * from the stage it forms n and psi = exp(-1/n) of the plane into a ring
+//   * from the stage it forms n and psi (exp(-1/n) or psi_eps) of the plane into a ring
 //     of 2R+2 planes (the halo psi is recomputed from populations the
 //     neighbouring tiles read too, so those reads hit L2);
 //   * then it collides plane zz - R: stencil force from the ring, the node's
@@ -72,17 +72,18 @@ __device__ __forceinline__ void stage_plane(const float *__restrict__ A, float *
     }
 }
 
-template <int EXY>
-__device__ __forceinline__ float psi_from_stage(const float *stage, int node, float rho0, bool &bad) {
+template <int EXY, bool EPS>
+__device__ __forceinline__ float psi_from_stage(const float *stage, int node, const Params &p,
+                                                bool &bad) {
     float g[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) g[i] = stage[i * EXY + node];
-    const float n = dens(g) + rho0;
+    const float n = dens(g) + p.rho0;
     bad |= !(n > 0.f);
-    return psi32(n);
+    return psi_fused<EPS>(n, p.eps, p.inv_eps);
 }
 
-template <int R, int NG>
+template <int R, int NG, bool EPS, bool F2>
 __global__ void __launch_bounds__(TX * TY, 2)
     k_fused3d(const float *__restrict__ A, float *__restrict__ B, const Params p, Flags *flags) {
     constexpr int EX = TX + 2 * R, EY = TY + 2 * R, NS = 2 * R + 2, EXY = EX * EY;
@@ -137,10 +138,10 @@ __global__ void __launch_bounds__(TX * TY, 2)
         cp_wait1();
         __syncthreads();
         float *slot = ring + (it % NS) * EXY;
-        slot[cen] = psi_from_stage<EXY>(cur, cen, p.rho0, bad);
+        slot[cen] = psi_from_stage<EXY, EPS>(cur, cen, p, bad);
         if (has_halo) {
             bool dummy = false;
-            slot[hof] = psi_from_stage<EXY>(cur, hof, p.rho0, dummy);
+            slot[hof] = psi_from_stage<EXY, EPS>(cur, hof, p, dummy);
         }
         __syncthreads();
         if (it < 2 * R) continue;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
         float F[3];
         force_ring<R, NG, EX>(pz, p, F);
         float out[19];
-        collide19(g, dens(g), F, p, out);
+        collide19<F2>(g, dens(g), F, p, out);
         if (owner) store19(B, p, xi, yi, zc, out);
     }
     if (bad) atomicMin(&flags->err_step, flags->step);
@@ -168,11 +169,36 @@ constexpr int smem_bytes() {
     return (2 * R + 2 + 2 * 19) * (TX + 2 * R) * (TY + 2 * R) * 4;
 }
 
+template <int R, int NG, bool EPS, bool F2>
+void launch1(dim3 grid, dim3 block, const float *A, float *B, const Params &p, lb_ctx *c) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_fused3d<R, NG, EPS, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<R>());
+        attr_done = true;
+    }
+    k_fused3d<R, NG, EPS, F2><<<grid, block, smem_bytes<R>(), c->stream>>>(A, B, p, c->flags);
+}
+
+// the instantiation for the stencil's widest group (ng = 1..7), the psi kind
+// and the forcing variant
+template <bool EPS, bool F2>
+void launch(int ng, dim3 grid, dim3 block, const float *A, float *B, const Params &p, lb_ctx *c) {
+    switch (ng) {
+        case 1: launch1<1, 1, EPS, F2>(grid, block, A, B, p, c); break;
+        case 2: launch1<1, 2, EPS, F2>(grid, block, A, B, p, c); break;
+        case 3: launch1<1, 3, EPS, F2>(grid, block, A, B, p, c); break;
+        case 4: launch1<2, 4, EPS, F2>(grid, block, A, B, p, c); break;
+        case 5: launch1<2, 5, EPS, F2>(grid, block, A, B, p, c); break;
+        case 6: launch1<2, 6, EPS, F2>(grid, block, A, B, p, c); break;
+        default: launch1<2, 7, EPS, F2>(grid, block, A, B, p, c); break;
+    }
+}
+
 }  // namespace fz
 
 bool fused3d_applicable(const lb_ctx *c, float *W, int *ng) {
-    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 19 || c->p.psi_kind != LB_PSI_EXP ||
-        c->p.forcing_A != 0.0)
+    if (c->p.precision != LB_FP32_SHIFTED || c->Q != 19)
         return false;
     if (c->g.nx < 8 || c->g.ny < 8 || c->g.nz < 8) return false;
     if ((long long)19 * c->g.Np >= (1LL << 31)) return false;
@@ -209,14 +235,19 @@ fc::Params fused_params(const lb_ctx *c, const float *W) {
     p.M2 = (float)M2;
     const double om = c->k.omega;
     p.omega = (float)om;
-    p.keep = (float)(1.0 - om);
+    p.keep = c->k.keep32;
     p.mGp = (float)c->k.mGp;
     p.rho0 = (float)c->k.rho0;
+    p.eps = c->k.psi_kind == LB_PSI_EPS ? (float)c->k.psi_eps : 0.f;
+    p.inv_eps = c->k.psi_kind == LB_PSI_EPS ? (float)c->k.psi_inv : 0.f;
     const double pref = 1.0 - 1.0 / (2.0 * c->p.tau);
     const double wc[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    const double kA = c->k.kA;
+    p.mhkA = (float)(-0.5 * kA);
     for (int k = 0; k < 3; ++k) {
         const double cw = pref * wc[k];
-        p.omw[k] = (float)(om * wc[k]);
+        p.kq[k] = (float)(-4.5 * cw * kA);
+        p.omw[k] = c->k.omw32[k];   // mass-exact with keep
         p.m3cw[k] = (float)(-3.0 * cw);
         p.b45[k] = (float)(4.5 * om * wc[k]);
         p.d3[k] = (float)(3.0 * om * wc[k]);
@@ -244,28 +275,16 @@ cudaError_t f32_fused3d_step(lb_ctx *c, const float *W, int ng) {
               (c->g.nz + p.zchunk - 1) / p.zchunk);
     const float *A = (const float *)c->f[c->cur];
     float *B = (float *)c->f[1 - c->cur];
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(fz::k_fused3d<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<1>());
-        cudaFuncSetAttribute(fz::k_fused3d<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<1>());
-        cudaFuncSetAttribute(fz::k_fused3d<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<1>());
-        cudaFuncSetAttribute(fz::k_fused3d<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
-        cudaFuncSetAttribute(fz::k_fused3d<2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
-        cudaFuncSetAttribute(fz::k_fused3d<2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
-        cudaFuncSetAttribute(fz::k_fused3d<2, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz::smem_bytes<2>());
-        attr_done = true;
-    }
-    const int sm1 = fz::smem_bytes<1>(), sm2 = fz::smem_bytes<2>();
     tm_begin(c, LB_KERNEL_FUSED);
-    switch (ng) {
-        case 1: fz::k_fused3d<1, 1><<<grid, block, sm1, c->stream>>>(A, B, p, c->flags); break;
-        case 2: fz::k_fused3d<1, 2><<<grid, block, sm1, c->stream>>>(A, B, p, c->flags); break;
-        case 3: fz::k_fused3d<1, 3><<<grid, block, sm1, c->stream>>>(A, B, p, c->flags); break;
-        case 4: fz::k_fused3d<2, 4><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
-        case 5: fz::k_fused3d<2, 5><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
-        case 6: fz::k_fused3d<2, 6><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
-        default: fz::k_fused3d<2, 7><<<grid, block, sm2, c->stream>>>(A, B, p, c->flags); break;
-    }
+    const bool eps = p.inv_eps != 0.f, f2 = c->k.kA != 0.0;
+    if (eps && f2)
+        fz::launch<true, true>(ng, grid, block, A, B, p, c);
+    else if (eps)
+        fz::launch<true, false>(ng, grid, block, A, B, p, c);
+    else if (f2)
+        fz::launch<false, true>(ng, grid, block, A, B, p, c);
+    else
+        fz::launch<false, false>(ng, grid, block, A, B, p, c);
     tm_end(c);
     c->launches += 1;
     c->cur = 1 - c->cur;

@@ -5,7 +5,8 @@
 // shared memory through the Tensor Memory Accelerator: one
 // cp.async.bulk.tensor per population (19 per plane, issued by one thread,
 // completed on an mbarrier) into a double-buffered stage, two planes ahead.
-// From the stage each thread forms n and psi = exp(-1/n) of its node (and of
+// From the stage each thread forms n and psi (exp(-1/n), or psi_eps of eq.
+// psieps in the EPS instantiation) of its node (and of
 // a halo node) into a psi plane, keeping its node's 19 pulled populations in
 // registers.  The stencil force is accumulated plane by plane in registers
 // (plane_force: one pass over a psi plane serves every target plane within
@@ -105,21 +106,6 @@ __device__ __forceinline__ void issue_plane(const CUtensorMap *map, float *stage
     }
 }
 
-// psi of extended node (ex, ey) of the tile from a stage
-template <int R>
-__device__ __forceinline__ float psi_from_boxes(const float *stage, int ex, int ey, float rho0,
-                                                bool &bad) {
-    float g[19];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const int cx = cvel<19>(i, 0);
-        g[i] = stage[i * box_stride<R>() + ey * BOXW + (ex + 4 - R - cx)];
-    }
-    const float n = dens(g) + rho0;
-    bad |= !(n > 0.f);
-    return psi32(n);
-}
-
 // Schedule of one CTA (it = 0 .. nit-1, plane zz = z0 - R + it, stage it & 1):
 //   wait stage(it); pulled populations of the own node -> registers, psi of
 //   the own and the halo node -> psi plane (it & 1); barrier (+ timeout vote);
@@ -128,7 +114,7 @@ __device__ __forceinline__ float psi_from_boxes(const float *stage, int ex, int 
 //   targets zz - R .. zz + R; collide target zz - R (complete now), store it.
 // The psi plane (it & 1) is rewritten at it + 2, after every thread has
 // passed the barrier of it + 1, i.e. finished reading it.
-template <int R, int NG>
+template <int R, int NG, bool EPS, bool F2>
 __global__ void __launch_bounds__(TX * TY, 2)
     k_fused3d_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ B, const Params p,
                   Flags *flags) {
@@ -192,15 +178,15 @@ __global__ void __launch_bounds__(TX * TY, 2)
             dq[PH] = dens(gq[PH]);
             const float n = dq[PH] + p.rho0, nh = dens(gh) + p.rho0;
             bad |= !(n > 0.f);
-            ps[2 * R] = psi32(n);
-            const float psh = psi32(nh);
+            ps[2 * R] = psi_fused<EPS>(n, p.eps, p.inv_eps);
+            const float psh = psi_fused<EPS>(nh, p.eps, p.inv_eps);
             pb[cen] = ps[2 * R];
             if (has_halo) pb[hof] = psh;
         } else {
             dq[PH] = dens(gq[PH]);
             const float n = dq[PH] + p.rho0;
             bad |= !(n > 0.f);
-            ps[2 * R] = psi32(n);
+            ps[2 * R] = psi_fused<EPS>(n, p.eps, p.inv_eps);
             pb[cen] = ps[2 * R];
         }
         if (!__syncthreads_and(ok)) {
@@ -234,7 +220,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
             F[1] = pre * acc[0][1];
             F[2] = pre * fz;
             float out[19];
-            collide19(gq[CS], dq[CS], F, p, out);
+            collide19<F2>(gq[CS], dq[CS], F, p, out);
             store19(B, p, xi, yi, z0 - 2 * R + it, out);
         }
         // advance the force and psi windows by one plane
@@ -272,6 +258,34 @@ __global__ void __launch_bounds__(TX * TY, 2)
 template <int R>
 constexpr int smem_bytes() {
     return (2 * 19 * box_stride<R>() + 2 * (TX + 2 * R) * (TY + 2 * R)) * 4 + 16;
+}
+
+template <int R, int NG, bool EPS, bool F2>
+void launch1(dim3 grid, dim3 block, const CUtensorMap &map, float *B, const Params &p, lb_ctx *c) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_fused3d_tma<R, NG, EPS, F2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<R>());
+        attr_done = true;
+    }
+    k_fused3d_tma<R, NG, EPS, F2><<<grid, block, smem_bytes<R>(), c->stream>>>(map, B, p, c->flags);
+}
+
+// the instantiation for the stencil's widest group (ng = 1..7), the psi kind
+// and the forcing variant; m1, m2: the tensor maps with boxes of TY + 2 and
+// TY + 4 rows
+template <bool EPS, bool F2>
+void launch(int ng, dim3 grid, dim3 block, const CUtensorMap &m1, const CUtensorMap &m2, float *B,
+            const Params &p, lb_ctx *c) {
+    switch (ng) {
+        case 1: launch1<1, 1, EPS, F2>(grid, block, m1, B, p, c); break;
+        case 2: launch1<1, 2, EPS, F2>(grid, block, m1, B, p, c); break;
+        case 3: launch1<1, 3, EPS, F2>(grid, block, m1, B, p, c); break;
+        case 4: launch1<2, 4, EPS, F2>(grid, block, m2, B, p, c); break;
+        case 5: launch1<2, 5, EPS, F2>(grid, block, m2, B, p, c); break;
+        case 6: launch1<2, 6, EPS, F2>(grid, block, m2, B, p, c); break;
+        default: launch1<2, 7, EPS, F2>(grid, block, m2, B, p, c); break;
+    }
 }
 
 }  // namespace ft
@@ -315,29 +329,17 @@ cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng) {
     dim3 block(fc::TX, fc::TY);
     dim3 grid(c->g.nx / fc::TX, c->g.ny / fc::TY, (c->g.nz + p.zchunk - 1) / p.zchunk);
     float *B = (float *)c->f[1 - c->cur];
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(ft::k_fused3d_tma<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<1>());
-        cudaFuncSetAttribute(ft::k_fused3d_tma<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<1>());
-        cudaFuncSetAttribute(ft::k_fused3d_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<1>());
-        cudaFuncSetAttribute(ft::k_fused3d_tma<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<2>());
-        cudaFuncSetAttribute(ft::k_fused3d_tma<2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<2>());
-        cudaFuncSetAttribute(ft::k_fused3d_tma<2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<2>());
-        cudaFuncSetAttribute(ft::k_fused3d_tma<2, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, ft::smem_bytes<2>());
-        attr_done = true;
-    }
-    const int sm1 = ft::smem_bytes<1>(), sm2 = ft::smem_bytes<2>();
     const CUtensorMap &m1 = c->tmap[c->cur][0], &m2 = c->tmap[c->cur][1];
     tm_begin(c, LB_KERNEL_FUSED);
-    switch (ng) {
-        case 1: ft::k_fused3d_tma<1, 1><<<grid, block, sm1, c->stream>>>(m1, B, p, c->flags); break;
-        case 2: ft::k_fused3d_tma<1, 2><<<grid, block, sm1, c->stream>>>(m1, B, p, c->flags); break;
-        case 3: ft::k_fused3d_tma<1, 3><<<grid, block, sm1, c->stream>>>(m1, B, p, c->flags); break;
-        case 4: ft::k_fused3d_tma<2, 4><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
-        case 5: ft::k_fused3d_tma<2, 5><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
-        case 6: ft::k_fused3d_tma<2, 6><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
-        default: ft::k_fused3d_tma<2, 7><<<grid, block, sm2, c->stream>>>(m2, B, p, c->flags); break;
-    }
+    const bool eps = p.inv_eps != 0.f, f2 = c->k.kA != 0.0;
+    if (eps && f2)
+        ft::launch<true, true>(ng, grid, block, m1, m2, B, p, c);
+    else if (eps)
+        ft::launch<true, false>(ng, grid, block, m1, m2, B, p, c);
+    else if (f2)
+        ft::launch<false, true>(ng, grid, block, m1, m2, B, p, c);
+    else
+        ft::launch<false, false>(ng, grid, block, m1, m2, B, p, c);
     tm_end(c);
     c->launches += 1;
     c->cur = 1 - c->cur;

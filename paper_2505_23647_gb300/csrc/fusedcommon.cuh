@@ -51,12 +51,25 @@ struct Params {
     int pplane;      // nxp * nyp
     int Np;          // population stride
     int zchunk;      // z planes per CTA
+    float eps, inv_eps;   // psi_eps: eps and RN(1/eps) in binary32 (0 for psi = exp(-1/n))
+    // F^2 variant (T = 2 u F - (A/tau) F F): -kA/2 and, per class, -4.5 cw kA
+    // (kA = A/tau; all 0 for Guo's T = 2 u F)
+    float mhkA, kq[3];
 };
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // psi = exp(-1/n) in binary32: correctly rounded reciprocal, then expf
 __device__ __forceinline__ float psi32(float n) { return expf(-__frcp_rn(n)); }
+
+// the pseudopotential of a fused kernel: EPS false psi = exp(-1/n), EPS true
+// psi_eps = (n/(eps + n))^(1/eps) (eq. psieps); both are the binary32
+// expressions of the generic path, so psi is the same value on every path
+template <bool EPS>
+__device__ __forceinline__ float psi_fused(float n, float eps, float inv_eps) {
+    if constexpr (EPS) return powf(n / (eps + n), inv_eps);
+    else return psi32(n);
+}
 
 __device__ __forceinline__ float dens(const float *g) {
     // pairwise tree keeps the binary32 sum short
@@ -181,6 +194,10 @@ __device__ __forceinline__ void plane_force(const float *pc, float s0, const Par
 //   even part  E = omega w (base + 4.5 n (xi.u)^2) + cw (9 (xi.u)(xi.F) - 3 u.F)
 //   odd part   O = 3 omega w n (xi.u) + 3 cw (xi.F)
 // and out(xi) = (1 - omega) g(xi) + E + O, out(-xi) = (1 - omega) g(-xi) + E - O.
+// F2: the F^2 variant's extra source -cw kA (4.5 (xi.F)^2 - 1.5 F.F) (Sec. VI),
+// its F.F part folded into u.F (u.F - (kA/2) F.F) and its (xi.F)^2 part
+// added to each pair's even part.
+template <bool F2 = false>
 __device__ __forceinline__ void collide19(const float *g, float dn, const float *F, const Params &p,
                                           float *out) {
     const float n = dn + p.rho0;
@@ -195,7 +212,8 @@ __device__ __forceinline__ void collide19(const float *g, float dn, const float 
     const float uy = fmaf(0.5f, F[1], jy) * inv;
     const float uz = fmaf(0.5f, F[2], jz) * inv;
     const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    const float uF = fmaf(ux, F[0], fmaf(uy, F[1], uz * F[2]));
+    float uF = fmaf(ux, F[0], fmaf(uy, F[1], uz * F[2]));
+    if constexpr (F2) uF = fmaf(p.mhkA, fmaf(F[0], F[0], fmaf(F[1], F[1], F[2] * F[2])), uF);
     const float base = fmaf(-1.5f * n, uu, dn);
     out[0] = fmaf(p.keep, g[0], fmaf(p.omw[0], base, p.m3cw[0] * uF));
     const float a1 = fmaf(p.omw[1], base, p.m3cw[1] * uF);
@@ -205,7 +223,9 @@ __device__ __forceinline__ void collide19(const float *g, float dn, const float 
 #define SCLBM_PAIR(I, C, CU, CF)                                                \
     {                                                                           \
         const float cu = (CU), cF = (CF);                                       \
-        const float ev = fmaf(cu, fmaf(b##C, cu, p.c9[C] * cF), a##C);          \
+        float aq = a##C;                                                        \
+        if constexpr (F2) aq = fmaf(cF, p.kq[C] * cF, aq);                      \
+        const float ev = fmaf(cu, fmaf(b##C, cu, p.c9[C] * cF), aq);            \
         const float od = fmaf(e##C, cu, p.c3[C] * cF);                          \
         out[I] = fmaf(p.keep, g[I], ev + od);                                   \
         out[I + 1] = fmaf(p.keep, g[I + 1], ev - od);                           \

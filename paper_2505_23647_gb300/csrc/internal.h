@@ -1,6 +1,7 @@
 // internal.h -- context layout and kernel launchers shared by the library's
 // translation units (not part of the public ABI).
 #pragma once
+#include <cmath>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -38,7 +39,69 @@ struct Consts {
     double kA;      // A/tau of the F^2 forcing variant (0: Guo's T = 2 u F)
     int psi_kind;   // LB_PSI_EXP or LB_PSI_EPS
     double psi_eps, psi_inv;   // eps and RN(1/eps) of psi_eps
+    // binary32 forms that move no mass systematically (mass_exact_f32, set
+    // once at creation): the velocity weights (summing to 1 exactly), and the
+    // fused kernels' keep = 1 - omega with the per-class omega w of the
+    // classes |xi|^2 = 0, 1, 2 (keep + sum_c multiplicity_c omega w_c == 1)
+    float w32[19];
+    float keep32, omw32[3];
 };
+
+// Mass-exact binary32 constants.  A binary32 step's density coefficient is
+// sum_c mult[c] v[c] (+ keep = 1 - omega for BGK in the even/odd form of
+// the fused kernels); with each constant rounded on its own that sum misses
+// its exact value by a few 1e-8, the same way every step, and the lattice
+// mass drifts by as much per step.  mass_exact_f32 nudges v[1] and v[2] by
+// at most a few ulps and gives v[0] (multiplicity 1) the remainder, so that
+// sum_c mult[c] v[c] == target holds exactly (every term and partial sum is
+// exact in binary64).  Returns false, leaving v as it was, if no such
+// choice is found.
+inline float nudge_f32(float x, int k) {
+    for (; k > 0; --k) x = nextafterf(x, 1e30f);
+    for (; k < 0; ++k) x = nextafterf(x, -1e30f);
+    return x;
+}
+
+inline bool mass_exact_f32(float *v, const int *mult, double target) {
+    for (int radius = 0; radius <= 6; ++radius)
+        for (int k1 = -radius; k1 <= radius; ++k1)
+            for (int k2 = -radius; k2 <= radius; ++k2) {
+                if ((k1 < 0 ? -k1 : k1) != radius && (k2 < 0 ? -k2 : k2) != radius) continue;
+                const float v1 = nudge_f32(v[1], k1), v2 = nudge_f32(v[2], k2);
+                const double rest = target - (double)mult[1] * v1 - (double)mult[2] * v2;
+                const float v0 = (float)rest;
+                if ((double)v0 != rest) continue;
+                v[0] = v0;
+                v[1] = v1;
+                v[2] = v2;
+                return true;
+            }
+    return false;
+}
+
+// Consts::w32, keep32 and omw32 for a D2Q9 (Q = 9) or D3Q19 lattice, from
+// its binary64 weights and omega.  keep = 1 - omega is first put on a 2^-26
+// grid (a change of at most 7.5e-9 in the relaxation rate), which the
+// axis and diagonal classes' ulp steps can always compensate.
+inline void fill_mass_exact_f32(Consts &k, int Q) {
+    const double wc[3] = {k.w[0], k.w[1], k.w[Q - 1]};   // rest, axis, diagonal
+    const int mult[3] = {1, Q == 9 ? 4 : 6, Q == 9 ? 4 : 12};
+    float v[3] = {(float)wc[0], (float)wc[1], (float)wc[2]};
+    mass_exact_f32(v, mult, 1.0);
+    for (int i = 0; i < 19; ++i) {
+        k.w32[i] = 0.f;
+        if (i < Q)
+            for (int c = 0; c < 3; ++c)
+                if (k.w[i] == wc[c]) k.w32[i] = v[c];
+    }
+    const double g = 67108864.0;   // 2^26
+    const float keep = (float)(std::nearbyint((double)(float)(1.0 - k.omega) * g) / g);
+    float o[3] = {(float)(k.omega * wc[0]), (float)(k.omega * wc[1]), (float)(k.omega * wc[2])};
+    mass_exact_f32(o, mult, 1.0 - (double)keep);
+    k.keep32 = keep;
+    for (int c = 0; c < 3; ++c) k.omw32[c] = o[c];
+}
+
 
 struct Geom {
     int nx, ny, nz;

@@ -410,4 +410,19 @@ inline ConstsT<T> consts_as(const Consts &c) {
     return r;
 }
 
+// binary32: the velocity weights of mass_exact_f32 (Consts::w32)
+template <>
+inline ConstsT<float> consts_as<float>(const Consts &c) {
+    ConstsT<float> r;
+    for (int i = 0; i < 19; ++i) {
+        r.w[i] = c.w32[i];
+        r.cw[i] = (float)c.cw[i];
+    }
+    r.omega = (float)c.omega;
+    r.mGp = (float)c.mGp;
+    r.rho0 = (float)c.rho0;
+    r.kA = (float)c.kA;
+    return r;
+}
+
 }  // namespace sclbm

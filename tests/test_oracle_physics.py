@@ -339,3 +339,16 @@ def test_coexistence_refuses_a_non_root():
     integrand = df(m) / f(m) ** (eps + 1.0) * (p0 - P(m))
     area = np.sum(0.5 * (integrand[1:] + integrand[:-1]) * np.diff(m))
     assert abs(area) < 1e-9
+
+
+def test_psi_eps_bench_workload_constants():
+    """The psi_eps bubble the benchmark runs: eps from eq. eps_moments for the
+    E8 stencils' e4 = 4/7 (Table tab:e2n_values), G' = 1.1 G'_c of that psi,
+    and the coexistence pair of eq. SCMaxwell there."""
+    pe = L.PSI_EPS_BUBBLE
+    assert abs(pe["eps"] - A.epsilon_of_e4(4.0 / 7.0)) < 1e-15
+    f, df = A.psi_eps_fn(pe["eps"])
+    Gc, _ = A.critical_coupling(psi=f, dpsi=df)
+    assert abs(pe["Gp"] - 1.1 * Gc) < 1e-12
+    ng, nl, _ = A.coexistence(pe["Gp"], pe["eps"], psi=f, dpsi=df, guess=(0.4, 1.4))
+    assert abs(pe["n_gas"] - ng) < 1e-10 and abs(pe["n_liquid"] - nl) < 1e-10
