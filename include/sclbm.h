@@ -76,7 +76,8 @@ enum { LB_G_LITERAL = 0, LB_G_TIMES_CS2 = 1 };
  * eps = 14/29 with e4 = 4/5), evaluated in binary64 as
  * RN(RN(n/RN(eps+n))^RN(1/eps)) with a correctly rounded power.  The
  * shifted-binary32 paths (two-kernel, fused D3Q19 and D2Q9, batches) all form
- * psi_eps as powf(n / (eps + n), 1/eps) in binary32, so every FP32 path uses
+ * psi_eps as exp2f(RN(1/eps) * log2f(n / (eps + n))) in binary32 (the base
+ * lies in (0, 1); about 2e-7 relative to the exact power), so every FP32 path uses
  * the same psi; a batch may mix both kinds. */
 enum { LB_PSI_EXP = 0, LB_PSI_EPS = 1 };
 

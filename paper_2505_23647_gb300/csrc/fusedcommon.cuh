@@ -63,11 +63,13 @@ __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >
 __device__ __forceinline__ float psi32(float n) { return expf(-__frcp_rn(n)); }
 
 // the pseudopotential of a fused kernel: EPS false psi = exp(-1/n), EPS true
-// psi_eps = (n/(eps + n))^(1/eps) (eq. psieps); both are the binary32
-// expressions of the generic path, so psi is the same value on every path
+// psi_eps = (n/(eps + n))^(1/eps) (eq. psieps) as 2^((1/eps) log2(n/(eps + n)))
+// (the base lies in (0, 1); about 2e-7 relative against the exact power);
+// both are the binary32 expressions of the generic path, so psi is the same
+// value on every path
 template <bool EPS>
 __device__ __forceinline__ float psi_fused(float n, float eps, float inv_eps) {
-    if constexpr (EPS) return powf(n / (eps + n), inv_eps);
+    if constexpr (EPS) return exp2f(inv_eps * log2f(n / (eps + n)));
     else return psi32(n);
 }
 

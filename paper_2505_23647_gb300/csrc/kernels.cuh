@@ -84,7 +84,7 @@ __device__ __forceinline__ double psi_eval<double>(double n, const PsiK &pk,
 template <>
 __device__ __forceinline__ float psi_eval<float>(float n, const PsiK &pk, unsigned long long *) {
     if (pk.kind == 0) return expf(-1.0f / n);
-    return powf(n / ((float)pk.eps + n), (float)pk.inv);
+    return exp2f((float)pk.inv * log2f(n / ((float)pk.eps + n)));
 }
 
 template <typename T>
