@@ -1,6 +1,9 @@
 """Parity at the benchmark's full size and launch configuration: D3Q19, E8
 forcing stencil (92 vectors), 256^3 periodic box with a bubble of radius 40,
-shifted binary32 populations, G = -5, tau = 1.
+shifted binary32 populations, tau = 1: the main workload (psi = exp(-1/n),
+G = -5, 0.15 inside / 1.9 outside), the psi_eps bubble (eps = 10/31 at 1.1
+G'_c from its coexistence pair) and the F^2 forcing run (A = 0.25) that
+bench.py also times.
 
 The oracle cannot step 16.7 M nodes in seconds, so it recomputes sampled
 nodes one at a time from the GPU's own state: after the GPU takes one more
@@ -20,11 +23,22 @@ P = pytest.importorskip("paper_2505_23647_gb300")
 NX = NY = NZ = 256
 
 
-@pytest.fixture(scope="module")
-def run():
-    rho = L.tanh_sphere(NX, NY, NZ, 40.0, 0.15, 1.9, 2.0)
+PE = L.PSI_EPS_BUBBLE
+# name: (inside, outside density, G' (literal), psi_eps, F^2 A)
+VARIANTS = {
+    "exp": (0.15, 1.9, -5.0, None, 0.0),
+    "psi_eps": (PE["n_gas"], PE["n_liquid"], PE["Gp"], PE["eps"], 0.0),
+    "f2": (0.15, 1.9, -5.0 / 3.0, None, 0.25),
+}
+
+
+@pytest.fixture(scope="module", params=list(VARIANTS))
+def run(request):
+    rin, rout, Gp, eps, A = VARIANTS[request.param]
+    rho = L.tanh_sphere(NX, NY, NZ, 40.0, rin, rout, 2.0)
     lat = P.Lattice("D3Q19", (NX, NY, NZ), rho, L.E8_3D.bases, L.E8_3D.weights,
-                    precision="fp32", tau=1.0, G=-5.0)
+                    precision="fp32", tau=1.0, G=Gp, psi_eps=eps, forcing_A=A)
+    assert P.lb_fused_active(lat.ctx) == 2      # the TMA kernel the bench times
     ob0 = lat.observables()
     lat.step(3)
     f3 = lat.state()
@@ -32,7 +46,7 @@ def run():
     f4 = lat.state()
     ob4 = lat.observables()
     lat.close()
-    return f3, f4, ob0, ob4
+    return f3, f4, ob0, ob4, (Gp, eps, A)
 
 
 def _samples():
@@ -50,8 +64,9 @@ def _samples():
 
 
 def test_sampled_nodes_match_oracle(run):
-    f3, f4, _, _ = run
-    o = oracle.Oracle("D3Q19", (NZ, NY, NX), L.E8_3D.groups, tau=1.0, G=-5.0)
+    f3, f4, _, _, (Gp, eps, A) = run
+    o = oracle.Oracle("D3Q19", (NZ, NY, NX), L.E8_3D.groups, tau=1.0, G=Gp,
+                      psi_kind=0 if eps is None else 1, psi_eps=eps or 0.0, forcing_A=A)
     o.f = f3                      # GPU state at step 3 (widened to binary64)
     worst = 0.0
     for (x, y, z) in _samples():
@@ -64,7 +79,7 @@ def test_sampled_nodes_match_oracle(run):
 
 
 def test_mass_conserved_at_full_size(run):
-    _, _, ob0, ob4 = run
+    _, _, ob0, ob4, _ = run
     assert ob0["status"] == P.LB_OK and ob4["status"] == P.LB_OK
     assert abs(ob4["mass"] - ob0["mass"]) < 1e-6 * ob0["mass"]
     assert ob4["rho_min"] > 0.0
