@@ -19,6 +19,8 @@
 // reference within binary32 rounding (tested), not bit for bit.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "fusedcommon.cuh"
 
 namespace sclbm {
@@ -171,11 +173,14 @@ constexpr int smem_bytes() {
 
 template <int R, int NG, bool EPS, bool F2>
 void launch1(dim3 grid, dim3 block, const float *A, float *B, const Params &p, lb_ctx *c) {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<unsigned long long> attr_done{0};   // devices done, one bit each
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ULL << (dev & 63);
+    if (!(attr_done.load() & bit)) {
         cudaFuncSetAttribute(k_fused3d<R, NG, EPS, F2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_bytes<R>());
-        attr_done = true;
+        attr_done.fetch_or(bit);
     }
     k_fused3d<R, NG, EPS, F2><<<grid, block, smem_bytes<R>(), c->stream>>>(A, B, p, c->flags);
 }

@@ -28,6 +28,8 @@
 // other copy, and leaves the step; lb_sync reports LB_ECUDA.
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cudaTypedefs.h>
 
 #include "fusedcommon.cuh"
@@ -262,11 +264,14 @@ constexpr int smem_bytes() {
 
 template <int R, int NG, bool EPS, bool F2>
 void launch1(dim3 grid, dim3 block, const CUtensorMap &map, float *B, const Params &p, lb_ctx *c) {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static std::atomic<unsigned long long> attr_done{0};   // devices done, one bit each
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ULL << (dev & 63);
+    if (!(attr_done.load() & bit)) {
         cudaFuncSetAttribute(k_fused3d_tma<R, NG, EPS, F2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<R>());
-        attr_done = true;
+        attr_done.fetch_or(bit);
     }
     k_fused3d_tma<R, NG, EPS, F2><<<grid, block, smem_bytes<R>(), c->stream>>>(map, B, p, c->flags);
 }
