@@ -226,9 +226,12 @@ long long lb_kernel_launches(const lb_ctx *ctx);
 
 /* Options of lb_set_option. */
 enum {
-    LB_OPT_FUSED = 1,   /* 1 (default): D3Q19 shifted-FP32 steps use the fused
-                           single-pass kernel when the stencil's groups are
-                           among the E8 groups and each dimension is >= 8;
+    LB_OPT_FUSED = 1,   /* 1 (default): shifted-FP32 steps use the fused
+                           single-pass kernels: D3Q19 when the stencil's
+                           groups are among the E8 groups and each dimension
+                           is >= 8, D2Q9 when they are among the 2D groups
+                           up to (2,2) and each dimension is >= 4 (either
+                           pseudopotential, either forcing variant);
                            0: always the two-kernel path */
     LB_OPT_ZCHUNK = 2,  /* z planes marched by one CTA of the fused kernel
                            (default 16) */

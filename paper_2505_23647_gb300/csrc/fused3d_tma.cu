@@ -164,6 +164,10 @@ __global__ void __launch_bounds__(TX * TY, 2)
     for (int k = 0; k <= 2 * R; ++k) acc[k][0] = acc[k][1] = acc[k][2] = ps[k] = 0.f;
     bool timed_out = false;
 
+    // unrolled by 2: the stage and psi-plane parity (it & 1) becomes a
+    // compile-time constant in each copy (measured 0.8-1.3 % faster; by 4 the
+    // code no longer fits the instruction cache, 10 % slower)
+#pragma unroll 2
     for (int it = 0; it < nit; ++it) {
         constexpr int PH = R, CS = 0;             // slots of planes zz and zz - R
         const int b = it & 1;
