@@ -7,7 +7,7 @@
   give the same populations bit for bit (the tiling never changes what a
   node computes);
 * lb_batch_tune leaves the members' states and counters as they were;
-* the many-instance workload (64 seeded instances, 4.95 M nodes, one
+* the many-instance workload (64 seeded instances, 4.55 M nodes, one
   launch per step in a CUDA graph): sampled nodes recomputed by the oracle
   from the GPU's own state, and per-member mass conservation;
 * members that the batch cannot step are refused on the host.
@@ -158,7 +158,7 @@ def test_unsupported_members_are_refused():
 
 
 @pytest.fixture(scope="module")
-def c3():
+def many():
     """The many-instance workload: 64 seeded instances, FP32-shifted."""
     inst = L.batched_instances(64)
     lats, rhos = [], []
@@ -186,15 +186,15 @@ def c3():
     return out
 
 
-def test_c3_workload_sampled_nodes_match_oracle(c3):
-    assert c3["nodes"] > 4_000_000
+def test_64_instance_workload_sampled_nodes_match_oracle(many):
+    assert many["nodes"] > 4_000_000
     rng = np.random.default_rng(0xC3)
     worst = 0.0
-    for k in rng.choice(len(c3["inst"]), size=12, replace=False):
-        d = c3["inst"][k]
+    for k in rng.choice(len(many["inst"]), size=12, replace=False):
+        d = many["inst"][k]
         s = d["side"]
         o = oracle.Oracle("D2Q9", (1, s, s), d["stencil"].groups, tau=1.0, G=G, convention=CONV)
-        o.f = c3["f_pre"][k].reshape(9, -1).copy()
+        o.f = many["f_pre"][k].reshape(9, -1).copy()
         pts = [(0, 0), (s - 1, s - 1), (s // 2, s // 2)]
         pts += [tuple(int(v) for v in rng.integers(0, s, 2)) for _ in range(6)]
         r = d["radius"]
@@ -204,11 +204,11 @@ def test_c3_workload_sampled_nodes_match_oracle(c3):
         for x, y in pts:
             post = o.node_post(x, y)
             for i, c in enumerate(oracle.C9):
-                g = c3["f_post"][k][i, 0, (y + c[1]) % s, (x + c[0]) % s]
+                g = many["f_post"][k][i, 0, (y + c[1]) % s, (x + c[0]) % s]
                 worst = max(worst, abs(g - post[i]) / max(abs(post[i]), 1e-3))
     assert worst < 1e-5, worst
 
 
-def test_c3_workload_conserves_mass(c3):
-    for m0, m1 in zip(c3["m0"], c3["m1"]):
+def test_64_instance_workload_conserves_mass(many):
+    for m0, m1 in zip(many["m0"], many["m1"]):
         assert abs(m1 - m0) < 1e-6 * m0

@@ -42,7 +42,7 @@ def _run_pair(lattice, shape_xyz, stencil, rho, steps, precision="fp64", tau=1.0
 T3_2D = L.stencil_e4e6_tuning_8(2, Fr(-2, 3), Fr(1, 10))
 
 FP64_CASES = [
-    # C1 shape: D2Q9 E4, 256 x 4 flat slab from the tanh profile, 100 steps
+    # the 256 x 4 flat slab: D2Q9 E4, tanh profile, 100 steps
     ("D2Q9", (256, 4), L.E4_2D, "slab", 100, 1.0, -5.0, "literal"),
     ("D2Q9", (61, 47), L.E8_2D, "drop", 100, 0.8, -15.0, "paper"),
     ("D2Q9", (40, 37), T3_2D, "drop", 60, 1.3, -5.0, "literal"),
