@@ -178,10 +178,14 @@ __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int
     const int nit = (y1 - y0) + 4;
     // the next row's populations are in flight while this row is computed
     float gn[9], hn = 0.f, hn0 = 0.f;
+    int colN[9];                       // population and source-column part of each load
+#pragma unroll
+    for (int i = 0; i < 9; ++i) colN[i] = i * N + cs[cvel<9>(i, 0) + 1];
     auto pull = [&]() {
+        const float *Ar[3] = {A + rr[0], A + rr[1], A + rr[2]};   // the three source rows
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            gn[i] = __ldg(A + (i * N + rr[cvel<9>(i, 1) + 1] + cs[cvel<9>(i, 0) + 1]));
+            gn[i] = __ldg(Ar[cvel<9>(i, 1) + 1] + colN[i]);
         hn = __ldg(A + (hoff + (hcy == 0 ? rr[1] : (hcy < 0 ? rr[0] : rr[2]))));
         if (lane < 4) hn0 = __ldg(A + (rr[1] + hc));
     };
