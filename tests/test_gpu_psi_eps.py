@@ -48,6 +48,21 @@ def test_exp_kind_matches_oracle_bitwise():
     assert amb == 0 and np.array_equal(got, want)
 
 
+def test_exp_kind_many_densities_bitwise():
+    """300,000 seeded densities over the range the steps see (and beyond,
+    where exp(-1/n) leaves the table-driven first phase): the binary64 psi
+    equals the oracle's binary128 exp rounded once, bit for bit, whichever
+    phase of the library's exp answered."""
+    rng = np.random.default_rng(2024)
+    n = np.concatenate([rng.uniform(0.02, 6.0, 200_000),
+                        np.exp(rng.uniform(np.log(1e-3), np.log(1e4), 100_000))])
+    got, amb = P.lb_psi_eval(n)
+    want = np.array([oracle.psi(v) for v in n])
+    assert amb == 0
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(n[i], got[i], want[i]) for i in bad[:5]]
+
+
 def _coupling(eps):
     f, df = A.psi_eps_fn(eps)
     Gc, _ = A.critical_coupling(psi=f, dpsi=df)
