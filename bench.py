@@ -399,6 +399,78 @@ def run_gb300(args, dist, rank, ws):
                 "hbm_frac": (2 * 19 * 8 + 16) * v64 * 1e6 / 1e9 / peak,
                 "step_kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt64.items() if v[1]}}
 
+    # the small binary64 slab: D2Q9, E4, 256 x 4, liquid slab x in [64, 192)
+    # (tanh width 2), 10,000 steps; launch-bound, stepped through the
+    # context's CUDA graph.  G' = -3 from its coexistence pair (0.456, 2.25):
+    # a 1.9 / 0.15 slab at G' = -5/3 drives the gas below zero
+    slab = None
+    if not args.no_small:
+        rho_s = L.tanh_slab(256, 4, 1, 64, 192, 0.456, 2.25, 2.0)
+        lats = P.Lattice("D2Q9", (256, 4), rho_s, L.E4_2D.bases, L.E4_2D.weights,
+                         precision="fp64", tau=1.0, G=-3.0, convention="literal",
+                         stream=stream.cuda_stream)
+        lats.step(100)
+        ks = 10000
+        l0 = lats.launches()
+        e0.record(stream)
+        lats.step(ks)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mss = e0.elapsed_time(e1)
+        oks = lats.sync() == P.LB_OK
+        slab = {"value": ks / (mss * 1e-3), "unit": "steps/s", "steps": ks,
+                "mlups": 1024 * ks / (mss * 1e3), "ms_per_step": mss / ks,
+                "launches_per_step": (lats.launches() - l0) / ks, "precision": "fp64",
+                "stable": oks}
+        lats.close()
+
+    # 20 droplet / bubble runs (R = 8 .. 48 in 256 x 256 boxes, E8): binary32
+    # as one batch, binary64 lattice by lattice.  G' = -3 from its coexistence
+    # pair (0.456, 2.25): droplets of 1.9 in gas of 0.15 at G' = -5/3 drive the
+    # gas below zero
+    drops = None
+    if not args.no_droplets:
+        radii = (8, 12, 16, 20, 24, 28, 32, 36, 40, 48)
+        rhos = [L.tanh_sphere(256, 256, 1, r, 2.25, 0.456, 2.0) for r in radii] + \
+               [L.tanh_sphere(256, 256, 1, r, 0.456, 2.25, 2.0) for r in radii]
+        nd = 20 * 256 * 256
+        l32 = [P.Lattice("D2Q9", (256, 256), r, L.E8_2D.bases, L.E8_2D.weights, precision="fp32",
+                         tau=1.0, G=-3.0, convention="literal", stream=stream.cuda_stream)
+               for r in rhos]
+        bd = P.Batch(l32, stream=stream.cuda_stream)
+        bd.tune(20)
+        bd.step(64)
+        kd = 1024
+        e0.record(stream)
+        bd.step(kd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msd = e0.elapsed_time(e1)
+        okd = bd.sync() == P.LB_OK
+        bd.close()
+        for l in l32:
+            l.close()
+        l64 = [P.Lattice("D2Q9", (256, 256), r, L.E8_2D.bases, L.E8_2D.weights, precision="fp64",
+                         tau=1.0, G=-3.0, convention="literal", stream=stream.cuda_stream)
+               for r in rhos]
+        for l in l64:
+            l.step(2)
+        k64d = 40
+        e0.record(stream)
+        for l in l64:
+            l.step(k64d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64d = e0.elapsed_time(e1)
+        ok64 = all(l.sync() == P.LB_OK for l in l64)
+        for l in l64:
+            l.close()
+        drops = {"fp32_batch": {"value": nd * kd / (msd * 1e3), "unit": "MLUPS", "steps": kd,
+                                "ms_per_step": msd / kd, "stable": okd},
+                 "fp64": {"value": nd * k64d / (ms64d * 1e3), "unit": "MLUPS", "steps": k64d,
+                          "ms_per_step": ms64d / k64d, "stable": ok64},
+                 "lattices": 20, "nodes": nd}
+
     # the many-instance 2D workload: 64 seeded D2Q9 droplets/bubbles of
     # uneven size (sides 64..512, mixed E4/E6/E8 stencils), one launch per
     # step for all of them, replayed from a CUDA graph; tile shape tuned.
@@ -506,7 +578,8 @@ def run_gb300(args, dist, rank, ws):
             "gpu_launches": launches, "fp64": fp64, "literal_g": lit, "psi_eps": peps,
             "f2_forcing": f2,
             "fused_kernel": fused,
-            "batched_2d": batched, "adjoint": adjoint,
+            "batched_2d": batched, "adjoint": adjoint, "slab_fp64": slab,
+            "droplets_2d": drops,
             "observables": {"mass": obs["mass"], "umax": obs["umax"],
                             "rho_min": obs["rho_min"], "rho_max": obs["rho_max"],
                             "stable": stable, "first_unstable_step": obs["error_step"]},
@@ -526,6 +599,8 @@ def main():
     ap.add_argument("--no-literal", action="store_true")
     ap.add_argument("--no-psi-eps", action="store_true")
     ap.add_argument("--no-f2", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-droplets", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--zchunk", type=int, default=0,
