@@ -135,7 +135,8 @@ __device__ __forceinline__ void collide9(const float *g, float dn, float Fx, flo
 // the three source rows advance by one row offset per row, so no load
 // computes a wrap.  Sizes that are not multiples of 32: lanes past the edge
 // work on the periodic image and store nothing.  Offsets are 32-bit
-// (9 nx ny < 2^31, checked when the path is chosen).
+// (9 nx ny < 2^31, checked when the path is chosen).  EPS: psi_eps instead
+// of exp(-1/n); F2: the F^2 forcing variant in the collision.
 template <bool EPS, bool F2>
 __device__ __forceinline__ void march(const Inst &I, int x0, int y0, int y1, int parity,
                                       float *row, int lane) {
