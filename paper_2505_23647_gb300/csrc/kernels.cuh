@@ -165,11 +165,18 @@ __device__ __forceinline__ void force_acc(const T *__restrict__ psi, const Geom 
         const int e[3] = {e0, e1, e2};
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) {
+            // c t is exact for |c| <= 2 (2t = t + t), so acc + c t rounds the
+            // same whichever form computes it; t + t keeps the integer-to-
+            // floating conversion of c off the binary64 pipe
             const int c = e[mu];
             if (c == 1)
                 acc[mu] = acc[mu] + t;
             else if (c == -1)
                 acc[mu] = acc[mu] - t;
+            else if (c == 2)
+                acc[mu] = acc[mu] + (t + t);
+            else if (c == -2)
+                acc[mu] = acc[mu] - (t + t);
             else if (c != 0)
                 acc[mu] = acc[mu] + t * T(c);
         }
