@@ -383,7 +383,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     c->cur = 0;
     c->fused_enabled = true;
     c->fused_tma = true;
-    c->fused_zchunk = 16;
+    c->fused_zchunk = 18;
     auto fail = [&](lb_status s) {
         lb_destroy(c);
         return s;
