@@ -312,6 +312,30 @@ def run_gb300(args, dist, rank, ws):
         lit = {"value": N * 60 / (msl * 1e3), "unit": "MLUPS", "steps": 60, "warmup": 3,
                "stable": okl}
 
+    def time_variant(lat, steps):
+        """Time `steps` steps of a 3D variant of the workload after the warm-up:
+        throughput, the fused kernel's average time and its roofline fraction."""
+        fused_k = P.lb_fused_active(lat.ctx)
+        lat.step(args.warmup)
+        P.lb_timing(lat.ctx, 1)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_v = e0.elapsed_time(e1)
+        kt_v = P.lb_timing_read(lat.ctx)
+        P.lb_timing(lat.ctx, 0)
+        ok_v = lat.sync() == P.LB_OK
+        ob_v = lat.observables()
+        lat.close()
+        kms_v, kn_v = kt_v.get("fused", (0.0, 0))
+        return {"value": N * steps / (ms_v * 1e3), "unit": "MLUPS", "steps": steps,
+                "ms_per_step": ms_v / steps, "fused_kernel": fused_k,
+                "kernel_ms_avg": kms_v / kn_v if kn_v else None,
+                "hbm_frac": ALG_BYTES["fused"] * N / (kms_v / kn_v * 1e-3) / 1e9 / peak
+                if kn_v else None,
+                "stable": ok_v, "rho_min": ob_v["rho_min"], "rho_max": ob_v["rho_max"]}
+
     # the same bubble with psi_eps (eq. psieps; eps = 10/31 of the E8 stencil's
     # e4 by eq. eps_moments) at 1.1 times its critical coupling, started from
     # its coexistence pair: the fused kernel's psi_eps instantiation
@@ -319,32 +343,11 @@ def run_gb300(args, dist, rank, ws):
     if not args.no_psi_eps:
         pe = L.PSI_EPS_BUBBLE
         rho_e = L.tanh_sphere(NX, NY, NZ, RADIUS, pe["n_gas"], pe["n_liquid"], 2.0)
-        late = P.Lattice("D3Q19", (NX, NY, NZ), rho_e, L.E8_3D.bases, L.E8_3D.weights,
-                         precision="fp32", tau=1.0, G=pe["Gp"], convention="literal",
-                         psi_eps=pe["eps"], stream=stream.cuda_stream)
-        fused_e = P.lb_fused_active(late.ctx)
-        late.step(args.warmup)
-        ke = min(args.steps, 1000)
-        P.lb_timing(late.ctx, 1)
-        e0.record(stream)
-        late.step(ke)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mse = e0.elapsed_time(e1)
-        kte = P.lb_timing_read(late.ctx)
-        P.lb_timing(late.ctx, 0)
-        oke = late.sync() == P.LB_OK
-        obe = late.observables()
-        late.close()
-        kfe = kte.get("fused", (0.0, 0))
-        ve = N * ke / (mse * 1e3)
-        peps = {"value": ve, "unit": "MLUPS", "steps": ke, "ms_per_step": mse / ke,
-                "eps": pe["eps"], "Gp": pe["Gp"], "densities": [pe["n_gas"], pe["n_liquid"]],
-                "fused_kernel": fused_e,
-                "kernel_ms_avg": kfe[0] / kfe[1] if kfe[1] else None,
-                "hbm_frac": ALG_BYTES["fused"] * N / (kfe[0] / kfe[1] * 1e-3) / 1e9 / peak
-                if kfe[1] else None,
-                "stable": oke, "rho_min": obe["rho_min"], "rho_max": obe["rho_max"]}
+        peps = time_variant(P.Lattice("D3Q19", (NX, NY, NZ), rho_e, L.E8_3D.bases,
+                                      L.E8_3D.weights, precision="fp32", tau=1.0, G=pe["Gp"],
+                                      convention="literal", psi_eps=pe["eps"],
+                                      stream=stream.cuda_stream), min(args.steps, 1000))
+        peps.update({"eps": pe["eps"], "Gp": pe["Gp"], "densities": [pe["n_gas"], pe["n_liquid"]]})
 
     # the same bubble with the F^2 forcing variant (Sec. VI: T = 2 u F -
     # (A/tau) F F in eq. GuoForcing; the paper fixes no A, this uses 0.25):
@@ -352,30 +355,11 @@ def run_gb300(args, dist, rank, ws):
     f2 = None
     if not args.no_f2:
         A_f2 = 0.25
-        latf = P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), L.E8_3D.bases,
-                         L.E8_3D.weights, precision="fp32", tau=1.0, G=G, convention=CONVENTION,
-                         forcing_A=A_f2, stream=stream.cuda_stream)
-        fused_f = P.lb_fused_active(latf.ctx)
-        latf.step(args.warmup)
-        kf = min(args.steps, 1000)
-        P.lb_timing(latf.ctx, 1)
-        e0.record(stream)
-        latf.step(kf)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msf = e0.elapsed_time(e1)
-        ktf = P.lb_timing_read(latf.ctx)
-        P.lb_timing(latf.ctx, 0)
-        okf = latf.sync() == P.LB_OK
-        latf.close()
-        kff = ktf.get("fused", (0.0, 0))
-        vf = N * kf / (msf * 1e3)
-        f2 = {"value": vf, "unit": "MLUPS", "steps": kf, "ms_per_step": msf / kf, "A": A_f2,
-              "fused_kernel": fused_f,
-              "kernel_ms_avg": kff[0] / kff[1] if kff[1] else None,
-              "hbm_frac": ALG_BYTES["fused"] * N / (kff[0] / kff[1] * 1e-3) / 1e9 / peak
-              if kff[1] else None,
-              "stable": okf}
+        f2 = time_variant(P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), L.E8_3D.bases,
+                                    L.E8_3D.weights, precision="fp32", tau=1.0, G=G,
+                                    convention=CONVENTION, forcing_A=A_f2,
+                                    stream=stream.cuda_stream), min(args.steps, 1000))
+        f2["A"] = A_f2
 
     # FP64 path on the same workload (fewer steps; binary64 arithmetic)
     fp64 = None
