@@ -262,6 +262,32 @@ __device__ inline double exp_cr(double x, unsigned long long *ambiguous) {
 //   atanh(s) = s (1 + s^2/3 + s^4/5 + ...) summed to s^40 (truncation
 //   below 2^-106 relative) by Horner in double-double; ln2 in the three
 //   parts of exp_dd_cr (k L1, k L2 exact).
+// 1/(2j+1), j = 0..20, as double-double pairs (hi = RN(1/d), lo =
+// RN((1 - hi d)/d)); gen_exp_table.py
+__device__ const double ATANH_INV[21][2] = {
+    {0x1.0000000000000p+0, 0x0.0p+0},   // 1/1
+    {0x1.5555555555555p-2, 0x1.5555555555555p-56},   // 1/3
+    {0x1.999999999999ap-3, -0x1.999999999999ap-57},   // 1/5
+    {0x1.2492492492492p-3, 0x1.2492492492492p-57},   // 1/7
+    {0x1.c71c71c71c71cp-4, 0x1.c71c71c71c71cp-58},   // 1/9
+    {0x1.745d1745d1746p-4, -0x1.745d1745d1746p-59},   // 1/11
+    {0x1.3b13b13b13b14p-4, -0x1.3b13b13b13b14p-58},   // 1/13
+    {0x1.1111111111111p-4, 0x1.1111111111111p-60},   // 1/15
+    {0x1.e1e1e1e1e1e1ep-5, 0x1.e1e1e1e1e1e1ep-61},   // 1/17
+    {0x1.af286bca1af28p-5, 0x1.af286bca1af28p-59},   // 1/19
+    {0x1.8618618618618p-5, 0x1.8618618618618p-59},   // 1/21
+    {0x1.642c8590b2164p-5, 0x1.642c8590b2164p-60},   // 1/23
+    {0x1.47ae147ae147bp-5, -0x1.eb851eb851eb8p-61},   // 1/25
+    {0x1.2f684bda12f68p-5, 0x1.2f684bda12f68p-59},   // 1/27
+    {0x1.1a7b9611a7b96p-5, 0x1.1a7b9611a7b96p-61},   // 1/29
+    {0x1.0842108421084p-5, 0x1.0842108421084p-60},   // 1/31
+    {0x1.f07c1f07c1f08p-6, -0x1.f07c1f07c1f08p-61},   // 1/33
+    {0x1.d41d41d41d41dp-6, 0x1.0750750750750p-60},   // 1/35
+    {0x1.bacf914c1bad0p-6, -0x1.bacf914c1bad0p-60},   // 1/37
+    {0x1.a41a41a41a41ap-6, 0x1.0690690690690p-60},   // 1/39
+    {0x1.8f9c18f9c18fap-6, -0x1.f3831f3831f38p-61},   // 1/41
+};
+
 __device__ inline ddv log_dd(double r) {
     int k0 = 0;
     if (r < 0x1p-1022) {   // subnormal: scale into the normal range (exact)
@@ -285,18 +311,9 @@ __device__ inline ddv log_dd(double r) {
     const ddv s = dd_fast_two_sum(q1, q2);
     const ddv s2 = dd_mul(s, s);
     // Horner: t = 1/41, t = 1/(2j+1) + s2 t, j = 19 .. 0
-    ddv t = ddv{__ddiv_rn(1.0, 41.0), 0.0};
-    {
-        const double h = t.hi;
-        t.lo = __ddiv_rn(__fma_rn(-h, 41.0, 1.0), 41.0);
-    }
-#pragma unroll 1
-    for (int j = 19; j >= 0; --j) {
-        const double d = (double)(2 * j + 1);
-        const double h = __ddiv_rn(1.0, d);
-        const ddv inv = ddv{h, __ddiv_rn(__fma_rn(-h, d, 1.0), d)};
-        t = dd_add(inv, dd_mul(s2, t));
-    }
+    ddv t = ddv{ATANH_INV[20][0], ATANH_INV[20][1]};
+#pragma unroll
+    for (int j = 19; j >= 0; --j) t = dd_add(ddv{ATANH_INV[j][0], ATANH_INV[j][1]}, dd_mul(s2, t));
     ddv at = dd_mul(s, t);                                  // atanh(s)
     at = ddv{__dmul_rn(at.hi, 2.0), __dmul_rn(at.lo, 2.0)}; // ln m
     const double L1 = 0x1.62e42fee00000p-1;

@@ -1,8 +1,9 @@
-"""Print the constants of the quick phase of exp_cr (expcr.cuh): the table
+"""Print the constants of expcr.cuh: for the quick phase of exp_cr the table
 2^(j/64), j = 0..63, as double-double pairs (hi = RN(2^(j/64)),
 lo = RN(2^(j/64) - hi)), and ln2/64 split for a Cody-Waite reduction (C1
 with 32 significant bits, so that k C1 is exact for |k| < 2^21; C2 =
-RN(ln2/64 - C1)), and RN(64/ln2).  Evaluated with 80 significant digits
+RN(ln2/64 - C1)), and RN(64/ln2); for log_dd the reciprocals 1/(2j+1),
+j = 0..20, as double-double pairs.  Evaluated with 80 significant digits
 (mpmath).  Run: python gen_exp_table.py > table.txt and paste."""
 import mpmath
 
@@ -30,6 +31,13 @@ def main():
     print(f"C1 = {float.hex(rn(c1))}")
     print(f"C2 = {float.hex(c2)}")
     print(f"INV = {float.hex(rn(64 / mpmath.log(2)))}")
+    # the reciprocals 1/(2j+1) of log_dd's atanh series: hi = RN(1/d),
+    # lo = RN((1 - hi d)/d) (the exact residual rounded once)
+    for j in range(21):
+        d = 2 * j + 1
+        hi = rn(mpmath.mpf(1) / d)
+        lo = rn((1 - mpmath.mpf(hi) * d) / d)
+        print(f"    {{{float.hex(hi)}, {float.hex(lo)}}},   // 1/{d}")
 
 
 if __name__ == "__main__":
