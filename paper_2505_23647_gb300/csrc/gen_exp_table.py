@@ -3,7 +3,8 @@
 lo = RN(2^(j/64) - hi)), and ln2/64 split for a Cody-Waite reduction (C1
 with 32 significant bits, so that k C1 is exact for |k| < 2^21; C2 =
 RN(ln2/64 - C1)), and RN(64/ln2); for log_dd the reciprocals 1/(2j+1),
-j = 0..20, as double-double pairs.  Evaluated with 80 significant digits
+j = 0..20, as double-double pairs; for the quick phase of pow_cr 1/F and
+ln F, F = 1 + j/128, j = 0..128, as double-double pairs.  Evaluated with 80 significant digits
 (mpmath).  Run: python gen_exp_table.py > table.txt and paste."""
 import mpmath
 
@@ -38,6 +39,15 @@ def main():
         hi = rn(mpmath.mpf(1) / d)
         lo = rn((1 - mpmath.mpf(hi) * d) / d)
         print(f"    {{{float.hex(hi)}, {float.hex(lo)}}},   // 1/{d}")
+    # the quick phase of pow_cr: F_j = 1 + j/128, j = 0..128, with 1/F_j and
+    # ln F_j as double-double pairs
+    for j in range(129):
+        F = 1 + mpmath.mpf(j) / 128
+        ih = rn(1 / F)
+        il = rn(1 / F - mpmath.mpf(ih))
+        lh = rn(mpmath.log(F))
+        ll = rn(mpmath.log(F) - mpmath.mpf(lh))
+        print(f"    {{{float.hex(ih)}, {float.hex(il)}, {float.hex(lh)}, {float.hex(ll)}}},   // F = 1 + {j}/128")
 
 
 if __name__ == "__main__":

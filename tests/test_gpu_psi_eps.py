@@ -48,6 +48,21 @@ def test_exp_kind_matches_oracle_bitwise():
     assert amb == 0 and np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("eps", [14.0 / 29.0, 10.0 / 31.0, 0.25, 2.0])
+def test_eps_kind_many_densities_bitwise(eps):
+    """60,000 seeded densities per eps: the binary64 psi_eps (a power of the
+    rounded base) equals the oracle's correctly rounded power bit for bit,
+    whichever phase of the library's power answered."""
+    rng = np.random.default_rng(77)
+    n = np.concatenate([rng.uniform(0.02, 6.0, 40_000),
+                        np.exp(rng.uniform(np.log(1e-3), np.log(1e3), 20_000))])
+    got, amb = P.lb_psi_eval(n, eps)
+    want = np.array([oracle.psi(v, 1, eps) for v in n])
+    assert amb == 0
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, [(n[i], got[i], want[i]) for i in bad[:5]]
+
+
 def test_exp_kind_many_densities_bitwise():
     """300,000 seeded densities over the range the steps see (and beyond,
     where exp(-1/n) leaves the table-driven first phase): the binary64 psi
