@@ -382,6 +382,28 @@ def run_gb300(args, dist, rank, ws):
         fp64 = {"value": v64, "unit": "MLUPS", "steps": k64, "ms_per_step": ms64 / k64,
                 "hbm_frac": (2 * 19 * 8 + 16) * v64 * 1e6 / 1e9 / peak,
                 "step_kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt64.items() if v[1]}}
+        # the psi_eps bubble in binary64: the correctly rounded power per node
+        if not args.no_psi_eps:
+            pe = L.PSI_EPS_BUBBLE
+            rho_e = L.tanh_sphere(NX, NY, NZ, RADIUS, pe["n_gas"], pe["n_liquid"], 2.0)
+            late = P.Lattice("D3Q19", (NX, NY, NZ), rho_e, L.E8_3D.bases, L.E8_3D.weights,
+                             precision="fp64", tau=1.0, G=pe["Gp"], convention="literal",
+                             psi_eps=pe["eps"], stream=stream.cuda_stream)
+            late.step(2)
+            late.sync()
+            P.lb_timing(late.ctx, 1)
+            e0.record(stream)
+            late.step(k64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mse = e0.elapsed_time(e1)
+            kte = P.lb_timing_read(late.ctx)
+            oke = late.sync() == P.LB_OK
+            late.close()
+            fp64["psi_eps"] = {"value": N * k64 / (mse * 1e3), "unit": "MLUPS", "steps": k64,
+                               "ms_per_step": mse / k64, "stable": oke,
+                               "step_kernels": {k: {"ms_total": v[0], "launches": v[1]}
+                                                for k, v in kte.items() if v[1]}}
 
     # the small binary64 slab: D2Q9, E4, 256 x 4, liquid slab x in [64, 192)
     # (tanh width 2), 10,000 steps; launch-bound, stepped through the
