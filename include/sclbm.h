@@ -224,6 +224,16 @@ lb_status lb_psi_eval(int psi_kind, double psi_eps, const double *n_in, double *
 /* Number of kernels this context has launched (for launch accounting). */
 long long lb_kernel_launches(const lb_ctx *ctx);
 
+/* Raw device counters of the context, read after the stream's work is done
+ * (synchronous), without judging them: out[0] the first step whose density
+ * check failed (-1: none), out[1] the steps the device has completed (the
+ * last block of each step advances it, also in a step whose waits gave up),
+ * out[2] binary64 roundings of psi that were not certified, out[3] blocks
+ * counted in the current fused step (0 between steps), out[4] mbarrier
+ * waits of the TMA kernel that gave up (sticky: every later lb_sync and
+ * lb_observables reports LB_ECUDA).  Diagnostics; LB_EINVAL for NULL. */
+lb_status lb_device_counters(lb_ctx *ctx, long long out[5]);
+
 /* Options of lb_set_option. */
 enum {
     LB_OPT_FUSED = 1,   /* 1 (default): shifted-FP32 steps use the fused
@@ -235,9 +245,16 @@ enum {
                            0: always the two-kernel path */
     LB_OPT_ZCHUNK = 2,  /* z planes marched by one CTA of the fused kernel
                            (default 18) */
-    LB_OPT_TMA = 3      /* 1 (default): on lattices with nx % 32 == 0,
+    LB_OPT_TMA = 3,     /* 1 (default): on lattices with nx % 32 == 0,
                            ny % 8 == 0, nz >= 8 the fused kernel stages planes
                            with TMA; 0: with per-thread cp.async */
+    LB_OPT_WAIT_POLLS = 5 /* bound on the tries of each mbarrier wait of the
+                           TMA kernel (default 2^26, range 0 .. 2^40).  A
+                           block whose wait runs out records it, lets its
+                           copies land and skips the rest of the step; the
+                           next lb_sync returns LB_ECUDA.  0 makes every
+                           wait give up at once (for testing that path); the
+                           state after such a step is not meaningful */
 };
 
 /* Set an option of the context.  LB_EINVAL for an unknown option or value. */
@@ -383,14 +400,20 @@ lb_status lb_adjoint_gradient(lb_adjoint *adj, double *dW, double *dG);
  * what they mean in lb_params.  The arithmetic and rounding order are those
  * of lb_step in LB_FP64 mode, so results are identical bit for bit.  Work is
  * enqueued on cuda_stream (NULL: the legacy default stream) and the call
- * returns without waiting.  No density check is reported.
+ * returns without waiting.  Nothing is reported back: neither the density
+ * check (n <= 0 or NaN) nor the count of binary64 exp roundings the step
+ * could not certify (which lb_observables reports as exp_ambiguous for a
+ * context); a caller that needs either steps a context with lb_step.
  *
  * The only scratch, the lattice's psi field and a few counters, lives in one
  * array of fixed size compiled into the library (LB_STATIC_MAX_NODES nodes):
  * every GPU that loads the library holds it until the process exits.  The
  * first call on a device looks up that array's device address (once per
  * device, with the device current); make that first call before any stream
- * capture.  All calls on a device share the array and it keeps the last
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that tears down and recreates the
+ * device's primary context) the kept address is stale, so do not call this
+ * entry point again in that process.  All calls on a device share the array and it keeps the last
  * call's contents: each call clears its counters and overwrites psi before
  * use, but two calls that overlap on the GPU (different streams, or
  * concurrent host threads) race on it and must be serialised by the caller.

@@ -82,6 +82,7 @@ _SIGS = {
     "lb_psi_eval": ([ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_longlong,
                      ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "lb_kernel_launches": ([_vp], ctypes.c_longlong),
+    "lb_device_counters": ([_vp, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "lb_timing": ([_vp, ctypes.c_int], ctypes.c_int),
     "lb_set_option": ([_vp, ctypes.c_int, ctypes.c_longlong], ctypes.c_int),
     "lb_step_fp64_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -291,7 +292,16 @@ def lb_kernel_launches(ctx):
     return int(_lib.lb_kernel_launches(_vp(ctx)))
 
 
-LB_OPT_FUSED, LB_OPT_ZCHUNK, LB_OPT_TMA = 1, 2, 3
+def lb_device_counters(ctx):
+    """Raw device counters: dict with error_step, device_step, exp_ambiguous,
+    blocks_done, timeouts."""
+    out = (ctypes.c_longlong * 5)()
+    _check(_lib.lb_device_counters(_vp(ctx), out), "lb_device_counters")
+    keys = ("error_step", "device_step", "exp_ambiguous", "blocks_done", "timeouts")
+    return dict(zip(keys, (int(v) for v in out)))
+
+
+LB_OPT_FUSED, LB_OPT_ZCHUNK, LB_OPT_TMA, LB_OPT_WAIT_POLLS = 1, 2, 3, 5
 
 
 def lb_set_option(ctx, option, value):

@@ -383,6 +383,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     c->cur = 0;
     c->fused_enabled = true;
     c->fused_tma = true;
+    c->wait_polls = 1LL << 26;
     c->fused_zchunk = 18;
     auto fail = [&](lb_status s) {
         lb_destroy(c);
@@ -634,6 +635,19 @@ lb_status lb_psi_eval(int psi_kind, double psi_eps, const double *n_in, double *
 
 long long lb_kernel_launches(const lb_ctx *c) { return c ? c->launches : 0; }
 
+lb_status lb_device_counters(lb_ctx *c, long long out[5]) {
+    if (!c || !out) return LB_EINVAL;
+    Flags h;
+    CK(cudaMemcpyAsync(&h, c->flags, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out[0] = h.err_step == ULLONG_MAX ? -1 : (long long)h.err_step;
+    out[1] = (long long)h.step;
+    out[2] = (long long)h.exp_amb;
+    out[3] = (long long)h.blocks_done;
+    out[4] = (long long)h.timeouts;
+    return LB_OK;
+}
+
 lb_status lb_set_option(lb_ctx *c, int option, long long value) {
     if (!c) return LB_EINVAL;
     switch (option) {
@@ -646,6 +660,10 @@ lb_status lb_set_option(lb_ctx *c, int option, long long value) {
         case LB_OPT_ZCHUNK:
             if (value < 1 || value > 1 << 20) return LB_EINVAL;
             c->fused_zchunk = (int)value;
+            return LB_OK;
+        case LB_OPT_WAIT_POLLS:
+            if (value < 0 || value > (1LL << 40)) return LB_EINVAL;
+            c->wait_polls = value;
             return LB_OK;
     }
     return LB_EINVAL;

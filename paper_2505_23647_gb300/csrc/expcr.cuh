@@ -468,14 +468,27 @@ __device__ const double LOG_F128[129][4] = {
 };
 
 // Quick phase of pow_cr: ln r = k ln2 + ln F + ln(1 + f) for r = 2^k m,
-// m in [1, 2), F = 1 + j/128 nearest to m (Tang's table-driven logarithm):
-// m - F is exact, f = (m - F)/F is formed in double-double from the
-// tabulated 1/F, and ln(1 + f) by its Taylor polynomial to degree 8
-// (|f| <= 2^-8: truncation below 2^-75).  The absolute error of the pair
-// is below 2^-68 (the degree-2 term's rounding; 2^-68.9 is the largest seen
-// over 40,000 arguments against a 250-bit evaluation); an absolute error of
-// the exponent e ln r is a relative error of r^e, so the exp quick phase
-// takes it as extra certification width (e 2^-67, with margin).
+// m in [1, 2), F = 1 + j/128 nearest to m (Tang's table-driven logarithm,
+// ACM TOMS 16(4), 1990): d = m - F is exact (|d| <= 2^-8), f = d/F is formed
+// in double-double from the tabulated 1/F, and ln(1 + f) = f + Q(f) with
+// Q(f) = sum_{k=2..8} (-1)^(k+1) f^k/k evaluated by Horner on f.hi.
+// Absolute error of the pair (ln(1 + f), the bound the certification uses):
+//   * truncation after degree 8: |f|^9/9 <= 2^-75.2;
+//   * f itself (fma rounding of d il + fe, table 1/F to 2^-106): 2^-113;
+//   * Q on f.hi instead of f: the first-order term -f.hi f.lo is added
+//     explicitly; what remains is f^2 |f.lo| <= 2^-16 2^-62 = 2^-78;
+//   * Q's roundings: |Q| <= f^2/2 <= 2^-17; the Horner value q ~ -1/2 is
+//     off by at most 2^-54 (its last fma; earlier steps enter times
+//     |f| <= 2^-8), i.e. 2^-53 relative, f.hi^2 and the product add 2^-53
+//     relative each: 3 2^-53 2^-17 = 3 2^-70;
+//   * the two roundings of the low-part sums (values below 2^-17): 2 2^-70;
+//   * k ln2 (split ln2 with exact k L1, k L2; k L3 rounded: 2^-107) and
+//     ln F (tabulated double-double, 2^-107), the double-double additions
+//     (relative 2^-104 of |l| <= 745): below 2^-94.
+// Total below 5 2^-70 = 2^-67.68 (2^-68.9 is the largest seen over 40,000
+// arguments against a 250-bit evaluation).  An absolute error of the
+// exponent e ln r is a relative error of r^e, so the exp quick phase takes
+// e 2^-67 (> e 2^-67.68) as extra certification width.
 __device__ __forceinline__ bool pow_quick(double r, double e, double *out) {
     if (!(r >= 0x1p-1022 && r < 0x1p1023 && e > 0.0 && e < 0x1p20)) return false;
     const long long bits = __double_as_longlong(r);

@@ -269,6 +269,7 @@ fc::Params fused_params(const lb_ctx *c, const float *W) {
     p.pplane = c->g.nxp * c->g.nyp;
     p.Np = (int)c->g.Np;
     p.zchunk = c->fused_zchunk > 0 ? c->fused_zchunk : 18;
+    p.max_polls = c->wait_polls;
     return p;
 }
 

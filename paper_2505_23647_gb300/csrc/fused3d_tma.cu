@@ -23,9 +23,10 @@
 // aligned start); the pull's x/y shift becomes a compile-time offset when the
 // box is read.  Requires nx % 32 == 0, ny % 8 == 0.
 //
-// Every wait on an mbarrier is bounded: after MAX_POLLS unsuccessful polls
-// the block records a timeout in the device counters, waits (bounded) for its
-// other copy, and leaves the step; lb_sync reports LB_ECUDA.
+// Every wait on an mbarrier is bounded (Params::max_polls tries, 2^26 by
+// default): a block whose wait gives up records a timeout in the device
+// counters, lets its copies in flight land, counts itself as finished and
+// leaves the step; lb_sync reports LB_ECUDA.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -41,7 +42,7 @@ namespace ft {
 using namespace fc;
 
 constexpr int BOXW = 40;                  // columns x0 - 4 .. x0 + 35
-constexpr long long MAX_POLLS = 1LL << 26;
+constexpr long long MAX_POLLS = 1LL << 26;   // default bound of a wait
 
 // floats between consecutive population boxes in a stage (boxes start on
 // 128-byte boundaries)
@@ -77,8 +78,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (long long k = 0; k < MAX_POLLS; ++k)
+// at most `polls` tries (0: gives up at once; used to test the timeout path)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  long long polls) {
+    for (long long k = 0; k < polls; ++k)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -91,6 +94,12 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
         "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
         "r"(smem_u32(bar))
         : "memory");
+}
+
+// order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
 // issue the 19 population boxes of plane zz into one stage
@@ -111,9 +120,10 @@ __device__ __forceinline__ void issue_plane(const CUtensorMap *map, float *stage
 // Schedule of one CTA (it = 0 .. nit-1, plane zz = z0 - R + it, stage it & 1):
 //   wait stage(it); pulled populations of the own node -> registers, psi of
 //   the own and the halo node -> psi plane (it & 1); barrier (+ timeout vote);
-//   the last thread refills stage(it) with plane zz + 2 (its readers are all
-//   behind the barrier); add this plane's force contributions to the 2R+1
-//   targets zz - R .. zz + R; collide target zz - R (complete now), store it.
+//   the issuing thread refills stage(it) with plane zz + 2 (its readers are
+//   all behind the barrier); add this plane's force contributions to the
+//   2R+1 targets zz - R .. zz + R; collide target zz - R (complete now),
+//   store it.
 // The psi plane (it & 1) is rewritten at it + 2, after every thread has
 // passed the barrier of it + 1, i.e. finished reading it.
 template <int R, int NG, bool EPS, bool F2>
@@ -128,6 +138,7 @@ __global__ void __launch_bounds__(TX * TY, 2)
     extern __shared__ __align__(128) float smem[];
     float *stage = smem;                          // two stages of 19 boxes
     float *pbuf = smem + 2 * STAGE;               // two psi planes (tile + halo)
+    // bar[0], bar[1]: the stages' copies landed
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(pbuf + 2 * EXY);
 
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
@@ -152,9 +163,12 @@ __global__ void __launch_bounds__(TX * TY, 2)
     }
     __syncthreads();
     const int nit = (z1 - z0) + 2 * R;
+    // issuing thread only: copies issued on / seen complete by it, per stage
+    int issued0 = 0, issued1 = 0, seen0 = 0, seen1 = 0;
     if (t == ISSUER) {
         issue_plane<R>(&map, stage, &bar[0], wrap1(z0 - R, p.nz), x0, y0, p);
         issue_plane<R>(&map, stage + STAGE, &bar[1], wrap1(z0 - R + 1, p.nz), x0, y0, p);
+        issued0 = issued1 = 1;
     }
     float gq[R + 1][19];        // pulled populations of planes zz - R .. zz
     float dq[R + 1];            // their shifted densities
@@ -171,7 +185,11 @@ __global__ void __launch_bounds__(TX * TY, 2)
     for (int it = 0; it < nit; ++it) {
         constexpr int PH = R, CS = 0;             // slots of planes zz and zz - R
         const int b = it & 1;
-        const bool ok = mbar_wait_bounded(&bar[b], (unsigned)(it >> 1) & 1u);
+        const bool ok = mbar_wait_bounded(&bar[b], (unsigned)(it >> 1) & 1u, p.max_polls);
+        if (t == ISSUER && ok) {
+            if (b) seen1 = (it >> 1) + 1;
+            else seen0 = (it >> 1) + 1;
+        }
         const float *st = stage + b * STAGE;
         float *pb = pbuf + b * EXY;
 #pragma unroll
@@ -200,10 +218,12 @@ __global__ void __launch_bounds__(TX * TY, 2)
             break;
         }
         if (t == ISSUER && it + 2 < nit) {
-            // the stage's readers are all behind the barrier above; order their
-            // generic-proxy reads before the async-proxy writes
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            // the stage's readers are all behind the barrier above; order
+            // their generic-proxy reads before the async-proxy writes
+            fence_proxy_async();
             issue_plane<R>(&map, stage + b * STAGE, &bar[b], wrap1(z0 - R + it + 2, p.nz), x0, y0, p);
+            if (b) ++issued1;
+            else ++issued0;
         }
         {   // this plane's share of the force on targets zz - R .. zz + R
             float cx[R + 1], cy[R + 1], cz[R + 1];
@@ -246,15 +266,18 @@ __global__ void __launch_bounds__(TX * TY, 2)
         }
     }
     if (__syncthreads_or(timed_out)) {
-        // a wait gave up (never expected): record it, give copies still in
-        // flight a bounded chance to land, and leave the step
+        // a wait gave up (never expected outside tests that set the bound to
+        // zero): record it, let every copy still in flight land so that no
+        // transfer touches this CTA's shared memory after it exits, then
+        // count the block as finished so the step counter stays consistent
         if (t == ISSUER) {
             atomicAdd(&flags->timeouts, 1ULL);
-            for (int k = 0; k < 2; ++k) {
-                mbar_wait_bounded(&bar[k], 0u);
-                mbar_wait_bounded(&bar[k], 1u);
-            }
+            for (; seen0 < issued0; ++seen0)
+                mbar_wait_bounded(&bar[0], (unsigned)seen0 & 1u, MAX_POLLS);
+            for (; seen1 < issued1; ++seen1)
+                mbar_wait_bounded(&bar[1], (unsigned)seen1 & 1u, MAX_POLLS);
         }
+        finish_step(flags, t);
         return;
     }
     if (bad) atomicMin(&flags->err_step, flags->step);

@@ -55,6 +55,7 @@ struct Params {
     // F^2 variant (T = 2 u F - (A/tau) F F): -kA/2 and, per class, -4.5 cw kA
     // (kA = A/tau; all 0 for Guo's T = 2 u F)
     float mhkA, kq[3];
+    long long max_polls;  // bound of every mbarrier wait of the TMA kernel
 };
 
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }

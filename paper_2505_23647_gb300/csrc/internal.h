@@ -144,6 +144,7 @@ struct lb_ctx {
     bool padded;              // populations carry periodic ghost columns/rows
     bool tma_ok;              // tensor maps built for the padded buffers
     bool fused_tma;           // option LB_OPT_TMA (default on)
+    long long wait_polls;     // option LB_OPT_WAIT_POLLS: bound of the TMA kernel's waits
     CUtensorMap tmap[2][2];   // [buffer][R-1] plane boxes of TY + 2R rows
     void *f[2];               // population buffers [Q][N] (post-collision, pre-stream)
     int cur;                  // buffer holding the current state

@@ -37,7 +37,10 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices];   // device address of g_scratch, per device
 
 // Device address of g_scratch on the current device (looked up once per
-// device; host code cannot use the symbol itself as a device pointer).
+// device; host code cannot use the symbol itself as a device pointer).  The
+// address belongs to the device's primary context: it does not survive
+// cudaDeviceReset, after which this entry point must not be used again in
+// the process.
 cudaError_t scratch_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -72,7 +75,7 @@ __global__ void k_static_psi(const double *__restrict__ f, double *__restrict__ 
 #pragma unroll
         for (int i = 0; i < Q; ++i) fi[i] = f[(long long)i * g.N + s];
         const double n = sum_q<double, Q>(fi);
-        psi[s] = psi_of<double>(n, &fl->exp_amb);
+        psi[s] = psi_of<double>(n, &fl->exp_amb);   // counted, not reported
     }
 }
 
