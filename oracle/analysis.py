@@ -15,8 +15,9 @@ Restates, in plain numpy/scipy, the paper's definitions:
 * z_s = first moment of P_N - P_T                           (eq. ZSDef)
 * z_e from Gamma(z_e) = 0, delta = z_e - z_s                 (eq. zemzs)
 * delta = Gamma(z_s) / (n_l - n_g)                          (eq. deltaads)
-* equimolar radius                                          (Sec. V B, Laplace)
-* generalized sigma[R] and the surface of tension           (Sec. III B)
+* equimolar radius R_e and the Laplace fit                  (Sec. V B, Laplace)
+* generalized sigma[R], the surface of tension R_s, sigma_s (Sec. III B)
+* curved Tolman length from Delta P R_s/((d-1) sigma0) vs 1/R_s (Sec. III B)
 
 Readings where the paper is silent (each used identically by the package's
 own post-processing):
@@ -26,7 +27,12 @@ own post-processing):
 * site x stands for the cell [x - 1/2, x + 1/2]; n_l and n_g are the measured
   densities at the liquid and gas ends of the window;
 * the x axis of a window is oriented from liquid to gas when forming delta
-  (the orientation that gives eq. SCTolmanFlat its sign).
+  (the orientation that gives eq. SCTolmanFlat its sign);
+* curved interfaces: P_T(r) is P^yy on the x axis through the centre, taken
+  at the sites and linear between them (the paper interpolates without
+  saying how), both rays (+x, -x) averaged, r from 0 to L/2; n_in is taken
+  at the centre, n_out at a corner site; droplets and bubbles share one
+  line in (-1)^b Delta P against the signed curvature (-1)^b / R.
 """
 from __future__ import annotations
 
@@ -220,9 +226,14 @@ def flat_sigma(P, n, D=2):
 
 # --- curved interfaces ----------------------------------------------------------
 def equimolar_radius(n, n_in, n_out):
-    """eq. (Laplace paragraph): pi R^2 n_in + (L^2 - pi R^2) n_out = M (2D), the
-    3D analogue with 4/3 pi R^3 (n_in is the inside density, droplet or
-    bubble)."""
+    """Equimolar radius R_e (Sec. V B, Laplace paragraph): the radius of the
+    sharp disc (d = 2) or sphere (d = 3) of density n_in in a background
+    n_out holding the lattice's total mass M:
+    pi R^2 n_in + (L^2 - pi R^2) n_out = M, or with 4/3 pi R^3 and L^3.
+    n_in is the inside density (liquid for a droplet, gas for a bubble);
+    the dimension is read from n's shape (nz, ny, nx): nz == 1 is 2D."""
+    if not n_in != n_out:
+        raise ValueError("equimolar_radius: n_in equals n_out (no interface)")
     M = float(np.sum(n))
     V = n.size
     if n.shape[0] == 1:
@@ -235,3 +246,151 @@ def laplace_fit(inv_R, dP):
     A = np.vstack([np.asarray(inv_R), np.ones(len(inv_R))]).T
     (slope, icpt), *_ = np.linalg.lstsq(A, np.asarray(dP), rcond=None)
     return float(slope), float(icpt)
+
+
+def _sample_line(field, center, D):
+    """Values of a site field (nz, ny, nx) along the x axis through `center`
+    (x, y[, z]), at the sites x = 0 .. nx-1: linear interpolation between the
+    neighbouring rows (and planes) when the centre's y (z) is not a site
+    coordinate.  Returns the x coordinates and the values."""
+    nz, ny, nx = field.shape
+    cy = float(center[1])
+    cz = float(center[2]) if D == 3 else 0.0
+    y0, z0 = int(np.floor(cy)), int(np.floor(cz))
+    ty, tz = cy - y0, cz - z0
+    line = np.zeros(nx)
+    for dz, wz in ((0, 1.0 - tz), (1, tz)):
+        if wz == 0.0:
+            continue
+        for dy, wy in ((0, 1.0 - ty), (1, ty)):
+            if wy == 0.0:
+                continue
+            line += wz * wy * field[(z0 + dz) % nz, (y0 + dy) % ny, :]
+    return np.arange(nx, dtype=np.float64), line
+
+
+def radial_profile(field, center, D):
+    """A site field along the ray from the centre in +x and in -x, r from 0
+    to L/2, as (r, value) for each ray: the field at sites, linearly
+    interpolated in x where the centre lies between sites (periodic)."""
+    xs, line = _sample_line(field, center, D)
+    nx = len(xs)
+    cx = float(center[0])
+    r_max = nx / 2.0
+    rays = []
+    for sgn in (1.0, -1.0):
+        # sample points: the centre, every site at 0 < r < L/2, and r = L/2
+        pts = [0.0]
+        k = np.arange(-nx, 2 * nx)
+        r_sites = sgn * (k - cx)
+        pts += sorted(r for r in r_sites if 0.0 < r < r_max)
+        pts.append(r_max)
+        r = np.array(pts)
+        x = cx + sgn * r
+        vals = np.interp(np.mod(x, nx), np.append(xs, nx), np.append(line, line[0]))
+        rays.append((r, vals))
+    return rays
+
+
+def generalized_sigma(R, r, PT, P_in, P_out, D):
+    """sigma[R] = int_0^{r_max} dr (r/R)^(d-1) [P_J(r; R) - P_T(r)] with
+    P_J = P_in for r < R and P_out beyond (Sec. III B, generalized surface
+    tension), for P_T given at the points r (0 .. r_max) and linear between
+    them: each piece's integral of r^(d-1) (a + b r) is taken in closed form,
+    the piece holding R split there."""
+    total = 0.0
+    for k in range(len(r) - 1):
+        ra, rb = float(r[k]), float(r[k + 1])
+        pa, pb = float(PT[k]), float(PT[k + 1])
+        b = (pb - pa) / (rb - ra)
+        a = pa - b * ra
+        cuts = [ra] + ([R] if ra < R < rb else []) + [rb]
+        for lo, hi in zip(cuts[:-1], cuts[1:]):
+            PJ = P_in if 0.5 * (lo + hi) < R else P_out
+            # int r^(d-1) (PJ - a - b r) dr from lo to hi
+            F = lambda t: (PJ - a) * t ** D / D - b * t ** (D + 1) / (D + 1)
+            total += F(hi) - F(lo)
+    return total / R ** (D - 1)
+
+
+def golden_min(fun, lo, hi, tol=1e-12, maxit=400):
+    """Minimum of a unimodal function on [lo, hi] by golden-section search."""
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    a, b = lo, hi
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = fun(c), fun(d)
+    for _ in range(maxit):
+        if b - a <= tol * max(1.0, abs(a) + abs(b)):
+            break
+        if fc < fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = fun(c)
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = fun(d)
+    x = 0.5 * (a + b)
+    return x, fun(x)
+
+
+def curved_observables(P, n, center, D, Gp, e2=1.0, psi=psi_exp, corner=(0, 0, 0)):
+    """Observables of one droplet or bubble at rest (Sec. III B, Sec. V B):
+
+    * n_in at the centre (linear interpolation), n_out at a corner site;
+      P_in, P_out their bulk pressures, Delta P = P_in - P_out;
+    * R_e, the equimolar radius;
+    * sigma[R] along the x axis through the centre with P_T = P^yy (both rays
+      averaged), its stationary point R_s (the surface of tension, where
+      d sigma[R]/dR = 0: a minimum, for droplets and bubbles alike, since
+      the inside pressure exceeds the outside one in both) and
+      sigma_s = sigma[R_s], by golden-section search over 0 < R < L/2.
+    P is the lattice pressure tensor (components of oracle.pressure_tensor,
+    (xx, xy, yy) in 2D, (xx, xy, xz, yy, yz, zz) in 3D)."""
+    nz, ny, nx = n.shape
+    cxyz = tuple(float(c) for c in center) + ((0.0,) if D == 2 else ())
+    _, nline = _sample_line(n, cxyz, D)
+    n_in = float(np.interp(cxyz[0], np.arange(nx + 1), np.append(nline, nline[0])))
+    n_out = float(n[corner[2] if D == 3 else 0, corner[1], corner[0]])
+    P_in = float(bulk_pressure(n_in, Gp, e2, psi))
+    P_out = float(bulk_pressure(n_out, Gp, e2, psi))
+    bubble = n_in < n_out   # b = 1
+    Pyy = P[2] if D == 2 else P[3]
+    rays = radial_profile(Pyy, cxyz, D)
+
+    def sigma(R):
+        return 0.5 * sum(generalized_sigma(R, r, v, P_in, P_out, D) for r, v in rays)
+    Rs, _ = golden_min(sigma, 0.5, nx / 2.0 - 0.5)
+    return {"n_in": n_in, "n_out": n_out, "P_in": P_in, "P_out": P_out,
+            "dP": P_in - P_out, "R_e": equimolar_radius(n, n_in, n_out),
+            "R_s": Rs, "sigma_s": sigma(Rs), "bubble": bool(bubble), "sigma_fn": sigma}
+
+
+def tolman_curved_fit(results, sigma0, D):
+    """The Tolman length from droplets and bubbles (Sec. III B): by eqs.
+    ExactLaplace and SigmaCExpansion, Delta P R_s / ((d-1) sigma0) =
+    1 - (d-1) delta / R_s with R_s counted negative for a bubble (b = 1);
+    a straight line through those points against (-1)^b / R_s has slope
+    -(d-1) delta.  Returns (delta, intercept)."""
+    x, y = [], []
+    for r in results:
+        s = -1.0 if r["bubble"] else 1.0
+        x.append(s / r["R_s"])
+        y.append(r["dP"] * r["R_s"] / ((D - 1) * sigma0))
+    slope, icpt = laplace_fit(x, y)
+    return -slope / (D - 1), icpt
+
+
+def laplace_sigma(results, D):
+    """sigma from the Laplace law over droplets and bubbles (Sec. V B): the
+    inside pressure exceeds the outside one for both (Delta P > 0); with the
+    factor (-1)^b on the pressure difference and on the curvature (b = 1 for
+    a bubble) both kinds lie on one line (-1)^b Delta P = (d-1) sigma
+    (-1)^b / R_e.  Returns (sigma, intercept)."""
+    x, y = [], []
+    for r in results:
+        s = -1.0 if r["bubble"] else 1.0
+        x.append(s / r["R_e"])
+        y.append(s * r["dP"])
+    slope, icpt = laplace_fit(x, y)
+    return slope / (D - 1), icpt
