@@ -120,6 +120,34 @@ typedef struct lb_obs {
                                 rounding boundary to certify (expected 0) */
 } lb_obs;
 
+/* One interface of a flat periodic slab (gradients along x), from the
+ * binary64 profiles of n, P_N = P^xx and P_T = P^yy averaged over y (and z).
+ * The window runs half way to the neighbouring interfaces; site x is the
+ * cell [x - 1/2, x + 1/2]; n_l, n_g are the profile's values at the
+ * window's liquid and gas ends. */
+typedef struct lb_flat_obs {
+    double sigma;       /* sum over the window of P_N - P_T (eq. sigma0pnpt) */
+    double z_s;         /* first moment of P_N - P_T (surface of tension, eq. ZSDef) */
+    double z_e;         /* equimolar surface, Gamma(z_e) = 0 */
+    double delta;       /* Tolman length z_e - z_s, x oriented liquid -> gas (eq. zemzs) */
+    double delta_ads;   /* Gamma(z_s) / (n_l - n_g) (eq. deltaads) */
+    double n_l, n_g;    /* bulk densities at the window's ends */
+    int window_lo, window_hi;  /* inclusive x range (may extend past 0 or nx-1: periodic) */
+    int rising;         /* 1: gas -> liquid along +x, 0: liquid -> gas */
+} lb_flat_obs;
+
+/* A droplet or bubble at rest, in binary64 (Sec. III B, Sec. V B). */
+typedef struct lb_curved_obs {
+    double n_in;        /* density at the centre (linear interpolation) */
+    double n_out;       /* density at the corner site (0, 0, 0) */
+    double P_in, P_out; /* bulk pressures n c_s^2 + (G' e2 / 2) psi(n)^2 */
+    double dP;          /* P_in - P_out (> 0 for droplets and bubbles alike) */
+    double R_e;         /* equimolar radius from the total mass */
+    double R_s;         /* surface of tension: d sigma[R] / dR = 0 */
+    double sigma_s;     /* sigma[R_s] = dP R_s / (d - 1) (eq. ExactLaplace) */
+    int bubble;         /* 1 if n_in < n_out (b = 1 of the (-1)^b sign) */
+} lb_curved_obs;
+
 typedef struct lb_ctx lb_ctx;
 
 /* Human-readable name of a status code (static storage). */
@@ -182,10 +210,14 @@ lb_status lb_step(lb_ctx *ctx, int nsteps);
  * since lb_create, else LB_OK (or LB_ECUDA). */
 lb_status lb_sync(lb_ctx *ctx);
 
-/* Observables of the current state with FP64 accumulation (compensated
- * double-double sums in a fixed order, rounded once): mass, momentum
- * sum(j + F/2), max |u|, min/max n.  Synchronous.  Returns LB_EUNSTABLE
- * (with *out filled) if a density check failed. */
+/* Observables of the current state, one fused pass over the populations
+ * with binary64 warp-shuffle reductions (compensated double-double sums in a
+ * fixed order, rounded once): mass, momentum sum(j + F/2), max |u|, min/max
+ * n.  Binary64 lattices: every node quantity in binary64.  Shifted-binary32
+ * lattices: n from the widened populations (to 2^-47 relative), F, u and
+ * j + F/2 in binary32 (the step's precision), the sums in binary64.
+ * Synchronous; allocates nothing.  Returns LB_EUNSTABLE (with *out filled)
+ * if a density check failed. */
 lb_status lb_observables(lb_ctx *ctx, lb_obs *out);
 
 /* Lattice pressure tensor (Appendices E and F) including the ideal part
@@ -195,6 +227,48 @@ lb_status lb_observables(lb_ctx *ctx, lb_obs *out);
  * the irregular (2,1[,0]), (2,1,1), (2,2,1); others give LB_EUNSUPPORTED.
  * Synchronous. */
 lb_status lb_pressure_tensor(lb_ctx *ctx, double *out);
+
+/* Interfaces of a flat periodic slab with gradients along x (Sec. III B,
+ * Sec. IV): the line integrals of the binary64 lattice pressure tensor over
+ * each interface's window -- sigma_0 (eq. sigma0pnpt), z_s (eq. ZSDef), z_e
+ * and the Tolman length delta = z_e - z_s (eq. zemzs), and Gamma(z_s) /
+ * (n_l - n_g) (eq. deltaads) -- computed on the device.  An interface lies
+ * between x and x + 1 where the y(z)-averaged density crosses
+ * (n_max + n_min) / 2.  out: host array of max_interfaces entries (filled in
+ * increasing x); *n_found: interfaces found (may exceed max_interfaces).
+ * Synchronous; allocates nothing (staging in the context's idle population
+ * buffer).  LB_EUNSUPPORTED for stencil groups outside Appendices E/F,
+ * LB_EINVAL for bad arguments or a lattice too narrow to stage the
+ * profiles. */
+lb_status lb_flat_interfaces(lb_ctx *ctx, int max_interfaces, lb_flat_obs *out,
+                             int *n_found);
+
+/* One droplet or bubble at rest centred at center (x, y[, z]; host, 2 or 3
+ * doubles, any real coordinates inside the box) (Sec. III B, Sec. V B):
+ * n_in at the centre, n_out at the corner site, their bulk pressures, the
+ * equimolar radius R_e (pi R_e^2 n_in + (L^2 - pi R_e^2) n_out = M, or the
+ * 3D analogue), and the surface of tension: along the x axis through the
+ * centre, with P_T = P^yy linear between the site samples on each ray (+x
+ * and -x, averaged) from r = 0 to L/2, the generalized surface tension
+ * sigma[R] = R^(1-d) int r^(d-1) (P_J(r; R) - P_T(r)) dr equals
+ * C R^(1-d) + dP R / d; its stationary point is R_s^d = d (d-1) C / dP with
+ * sigma_s = dP R_s / (d - 1).  All in binary64 on the device.  Synchronous;
+ * allocates nothing.  LB_EUNSUPPORTED for stencil groups outside
+ * Appendices E/F; LB_EINVAL for bad arguments. */
+lb_status lb_curved_interface(lb_ctx *ctx, const double *center, lb_curved_obs *out);
+
+/* The Laplace law over droplets and bubbles (Sec. V B): least-squares line
+ * through ((-1)^b / R_e, (-1)^b dP) of n results; *sigma = slope / (d - 1),
+ * *intercept its intercept.  Host arithmetic; LB_EINVAL for n < 2. */
+lb_status lb_fit_laplace(const lb_curved_obs *runs, int n, int dim, double *sigma,
+                         double *intercept);
+
+/* The Tolman length from droplets and bubbles (Sec. III B): least-squares
+ * line through ((-1)^b / R_s, dP R_s / ((d - 1) sigma0)) whose slope is
+ * -(d - 1) delta; writes *delta and the line's intercept (1 for an exact
+ * first-order expansion).  Host arithmetic; LB_EINVAL for n < 2. */
+lb_status lb_fit_tolman(const lb_curved_obs *runs, int n, int dim, double sigma0,
+                        double *delta, double *intercept);
 
 /* Density [N] and velocity u = (j + F/2)/n [D][N] of the current state
  * (either pointer may be NULL).  Synchronous. */

@@ -58,6 +58,21 @@ class lb_obs(ctypes.Structure):
                 ("error_step", ctypes.c_longlong), ("exp_ambiguous", ctypes.c_longlong)]
 
 
+class lb_flat_obs(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("z_s", ctypes.c_double), ("z_e", ctypes.c_double),
+                ("delta", ctypes.c_double), ("delta_ads", ctypes.c_double),
+                ("n_l", ctypes.c_double), ("n_g", ctypes.c_double),
+                ("window_lo", ctypes.c_int), ("window_hi", ctypes.c_int),
+                ("rising", ctypes.c_int)]
+
+
+class lb_curved_obs(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_double), ("n_out", ctypes.c_double),
+                ("P_in", ctypes.c_double), ("P_out", ctypes.c_double), ("dP", ctypes.c_double),
+                ("R_e", ctypes.c_double), ("R_s", ctypes.c_double),
+                ("sigma_s", ctypes.c_double), ("bubble", ctypes.c_int)]
+
+
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _vp = ctypes.c_void_p
@@ -75,6 +90,12 @@ _SIGS = {
     "lb_sync": ([_vp], ctypes.c_int),
     "lb_observables": ([_vp, ctypes.POINTER(lb_obs)], ctypes.c_int),
     "lb_pressure_tensor": ([_vp, _dp], ctypes.c_int),
+    "lb_flat_interfaces": ([_vp, ctypes.c_int, ctypes.POINTER(lb_flat_obs), _ip], ctypes.c_int),
+    "lb_curved_interface": ([_vp, _dp, ctypes.POINTER(lb_curved_obs)], ctypes.c_int),
+    "lb_fit_laplace": ([ctypes.POINTER(lb_curved_obs), ctypes.c_int, ctypes.c_int, _dp, _dp],
+                       ctypes.c_int),
+    "lb_fit_tolman": ([ctypes.POINTER(lb_curved_obs), ctypes.c_int, ctypes.c_int,
+                       ctypes.c_double, _dp, _dp], ctypes.c_int),
     "lb_get_fields": ([_vp, _dp, _dp], ctypes.c_int),
     "lb_get_state": ([_vp, _dp], ctypes.c_int),
     "lb_set_state": ([_vp, _dp], ctypes.c_int),
@@ -249,6 +270,55 @@ def lb_pressure_tensor(ctx, N, dim, out=None):
     out = np.empty((nc, N)) if out is None else out
     _check(_lib.lb_pressure_tensor(_vp(ctx), _ptr(out)), "lb_pressure_tensor")
     return out
+
+
+def _struct_dict(o):
+    return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def lb_flat_interfaces(ctx, max_interfaces=64):
+    """Per-interface dicts (sigma, z_s, z_e, delta, delta_ads, n_l, n_g,
+    window_lo, window_hi, rising) of a flat slab, computed on the device."""
+    out = (lb_flat_obs * max(1, max_interfaces))()
+    n = ctypes.c_int(0)
+    _check(_lib.lb_flat_interfaces(_vp(ctx), int(max_interfaces), out, ctypes.byref(n)),
+           "lb_flat_interfaces")
+    return [_struct_dict(out[i]) for i in range(min(n.value, max_interfaces))]
+
+
+def lb_curved_interface(ctx, center):
+    """Dict (n_in, n_out, P_in, P_out, dP, R_e, R_s, sigma_s, bubble) of a
+    droplet or bubble centred at `center` (x, y[, z]), computed on the device."""
+    c = np.ascontiguousarray(np.asarray(center, dtype=np.float64))
+    o = lb_curved_obs()
+    _check(_lib.lb_curved_interface(_vp(ctx), _ptr(c), ctypes.byref(o)), "lb_curved_interface")
+    d = _struct_dict(o)
+    d["bubble"] = bool(d["bubble"])
+    return d
+
+
+def _curved_array(runs):
+    arr = (lb_curved_obs * len(runs))()
+    for i, r in enumerate(runs):
+        for k, _ in lb_curved_obs._fields_:
+            setattr(arr[i], k, int(r[k]) if k == "bubble" else float(r[k]))
+    return arr
+
+
+def lb_fit_laplace(runs, dim):
+    """(sigma, intercept) of the Laplace law over curved-interface results."""
+    s, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.lb_fit_laplace(_curved_array(runs), len(runs), dim, ctypes.byref(s),
+                               ctypes.byref(b)), "lb_fit_laplace")
+    return s.value, b.value
+
+
+def lb_fit_tolman(runs, dim, sigma0):
+    """(delta, intercept) of the curved Tolman fit over curved-interface results."""
+    d, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.lb_fit_tolman(_curved_array(runs), len(runs), dim, float(sigma0), ctypes.byref(d),
+                              ctypes.byref(b)), "lb_fit_tolman")
+    return d.value, b.value
 
 
 def lb_get_fields(ctx, N, dim):
@@ -439,6 +509,12 @@ class Lattice:
 
     def pressure_tensor(self):
         return lb_pressure_tensor(self.ctx, self.N, self.D).reshape((-1,) + self.shape)
+
+    def flat_interfaces(self, max_interfaces=64):
+        return lb_flat_interfaces(self.ctx, max_interfaces)
+
+    def curved_interface(self, center):
+        return lb_curved_interface(self.ctx, center)
 
     def fields(self):
         rho, u = lb_get_fields(self.ctx, self.N, self.D)

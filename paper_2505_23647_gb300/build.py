@@ -1,7 +1,7 @@
 """Build the CUDA library in-tree: paper_2505_23647_gb300/_lib/libsclbm.so.
 
 Translation units are compiled in parallel with nvcc for sm_103a only:
-``fp64.cu`` and ``noalloc.cu`` with ``-fmad=false`` (binary64 expressions
+``fp64.cu``, ``noalloc.cu`` and ``observe.cu`` with ``-fmad=false`` (binary64 expressions
 round exactly as written, the documented FP64 order), the binary32 and API
 units with the defaults; the objects are linked into one shared library with the CUDA
 runtime linked statically.
@@ -27,6 +27,7 @@ UNITS = {
     "fused3d.cu": [],
     "fused3d_tma.cu": [],
     "noalloc.cu": ["-fmad=false"],
+    "observe.cu": ["-fmad=false"],
     "batch2d.cu": [],
     "adjoint.cu": [],
 }

@@ -442,7 +442,7 @@ lb_status lb_adjoint_zero_grad(lb_adjoint *a) {
 lb_status lb_adjoint_seed_sigma(lb_adjoint *a, int n_interfaces, double *sigma) {
     if (!a || n_interfaces < 1) return LB_EINVAL;
     lb_ctx *c = a->c;
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, a->lam2) : f32_get_state(c, a->lam2);
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, a->lam2, 0, c->Q) : f32_get_state(c, a->lam2, 0, c->Q);
     if (e != cudaSuccess) return afail(e, "lb_adjoint_seed_sigma state");
     lb_status s = fields_of(a, a->lam2);
     if (s != LB_OK) return s;
@@ -475,7 +475,7 @@ lb_status lb_adjoint_seed_pt(lb_adjoint *a, const double *m, double *value) {
     cudaError_t e = cudaMalloc(&dm, N * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpyAsync(dm, m, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = c->p.precision == LB_FP64 ? f64_get_state(c, a->lam2) : f32_get_state(c, a->lam2);
+        e = c->p.precision == LB_FP64 ? f64_get_state(c, a->lam2, 0, c->Q) : f32_get_state(c, a->lam2, 0, c->Q);
     if (e != cudaSuccess) {
         cudaFree(dm);
         return afail(e, "lb_adjoint_seed_pt");
@@ -520,7 +520,7 @@ lb_status lb_adjoint_run(lb_adjoint *a, int nsteps) {
     // forward: record the state before each step, then step
     for (int t = 0; t < nsteps; ++t) {
         double *st = a->states + (size_t)t * QN;
-        cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, st) : f32_get_state(c, st);
+        cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, st, 0, c->Q) : f32_get_state(c, st, 0, c->Q);
         if (e != cudaSuccess) return afail(e, "lb_adjoint_run record");
         lb_status s = lb_step(c, 1);
         if (s != LB_OK) return s;

@@ -204,17 +204,10 @@ void set_consts(lb_ctx *c) {
 
 size_t tsize(const lb_ctx *c) { return c->p.precision == LB_FP64 ? 8 : 4; }
 
-lb_status ensure_scratch(lb_ctx *c, size_t bytes) {
-    if (c->dscratch_bytes >= bytes) return LB_OK;
-    if (c->dscratch) {
-        CK(cudaStreamSynchronize(c->stream));
-        CK(cudaFree(c->dscratch));
-        c->dscratch = nullptr;
-        c->dscratch_bytes = 0;
-    }
-    CK(cudaMalloc(&c->dscratch, bytes));
-    c->dscratch_bytes = bytes;
-    return LB_OK;
+// populations of one state chunk that fit the staging buffer as binary64
+int stage_pops(lb_ctx *c) {
+    const long long per = (long long)(stage_bytes(c) / (sizeof(double) * (size_t)c->g.N));
+    return (int)(per < c->Q ? per : c->Q);
 }
 
 lb_status check_flags(lb_ctx *c, Flags *h) {
@@ -412,20 +405,21 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     Flags h0 = {ULLONG_MAX, 0, 0, 0, 0};
     e = cudaMemcpyAsync(c->flags, &h0, sizeof h0, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(flags)"));
-    lb_status s = ensure_scratch(c, (size_t)(1 + c->D) * N * sizeof(double));
-    if (s != LB_OK) return fail(s);
-    double *rho_d = c->dscratch, *u_d = u_init ? c->dscratch + N : nullptr;
-    e = cudaMemcpyAsync(rho_d, rho_init, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(rho)"));
-    if (u_init) {
-        e = cudaMemcpyAsync(u_d, u_init, c->D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(u)"));
-    }
     if (c->padded) {
         e = cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemset(f)"));
         c->tma_ok = tma_make_maps(c);
+    }
+    // the initial density (and velocity) are staged in the second population
+    // buffer, which the first step overwrites: no scratch allocation
+    if ((size_t)(1 + c->D) * N * sizeof(double) > stage_bytes(c)) return fail(LB_EINVAL);
+    double *rho_d = stage_ptr(c), *u_d = u_init ? rho_d + N : nullptr;
+    e = cudaMemcpyAsync(rho_d, rho_init, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(rho)"));
+    if (u_init) {
+        e = cudaMemcpyAsync(u_d, u_init, c->D * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(u)"));
     }
     e = p->precision == LB_FP64 ? f64_init(c, rho_d, u_d) : f32_init(c, rho_d, u_d);
     if (e != cudaSuccess) return fail(cuda_fail(e, "init kernel"));
@@ -442,7 +436,6 @@ lb_status lb_destroy(lb_ctx *c) {
     cudaFree(c->f[0]);
     cudaFree(c->f[1]);
     cudaFree(c->psi);
-    cudaFree(c->dscratch);
     cudaFree(c->red);
     cudaFree(c->flags);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -473,6 +466,7 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
         c->pairs32.w[a] = (float)w[a];
     }
     c->n_groups = (int)gb.size();
+    c->e2 = tmp.e2;
     for (size_t g = 0; g < gb.size(); ++g) {
         for (int k = 0; k < 3; ++k) c->group_base[g][k] = gb[g][k];
         c->group_w[g] = gw[g];
@@ -508,16 +502,10 @@ lb_status lb_sync(lb_ctx *c) {
 lb_status lb_observables(lb_ctx *c, lb_obs *out) {
     if (!c || !out) return LB_EINVAL;
     if (!c->stencil_set) return LB_ESTATE;
-    const long long N = c->g.N;
-    lb_status s = ensure_scratch(c, (size_t)(2 + 2 * c->D) * N * sizeof(double) + 16 * sizeof(double));
-    if (s != LB_OK) return s;
-    double *n = c->dscratch, *u = n + 2 * N, *mom = u + c->D * N, *res = mom + c->D * N;
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_fields(c, n, u, mom) : f32_fields(c, n, u, mom);
-    if (e != cudaSuccess) return cuda_fail(e, "fields kernels");
-    e = obs_reduce(c, n, u, mom, res);
-    if (e != cudaSuccess) return cuda_fail(e, "reduction kernels");
+    cudaError_t e = obs_fused(c);
+    if (e != cudaSuccess) return cuda_fail(e, "observables kernels");
     double h[7];
-    CK(cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(h, obs_results(c), sizeof h, cudaMemcpyDeviceToHost, c->stream));
     Flags f;
     lb_status st = check_flags(c, &f);
     if (st != LB_OK && st != LB_EUNSTABLE) return st;
@@ -537,16 +525,102 @@ lb_status lb_pressure_tensor(lb_ctx *c, double *out) {
     if (!c->stencil_set) return LB_ESTATE;
     const long long N = c->g.N;
     const int nc = c->D == 2 ? 3 : 6;
-    lb_status s = ensure_scratch(c, (size_t)(2 + nc) * N * sizeof(double));
-    if (s != LB_OK) return s;
-    double *n = c->dscratch, *psi = n + N, *P = psi + N;
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_density_psi(c, n, psi) : f32_density_psi(c, n, psi);
-    if (e != cudaSuccess) return cuda_fail(e, "density kernel");
-    e = ptensor(c, n, psi, P);
+    if ((size_t)(1 + nc) * N * sizeof(double) > stage_bytes(c)) return LB_EUNSUPPORTED;
+    double *psi = stage_ptr(c), *P = psi + N;
+    cudaError_t e = ptensor_field(c, psi, P);
     if (e == cudaErrorNotSupported) return LB_EUNSUPPORTED;
-    if (e != cudaSuccess) return cuda_fail(e, "pressure tensor kernel");
+    if (e != cudaSuccess) return cuda_fail(e, "pressure tensor kernels");
     CK(cudaMemcpyAsync(out, P, (size_t)nc * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_flat_interfaces(lb_ctx *c, int max_interfaces, lb_flat_obs *out, int *n_found) {
+    if (!c || max_interfaces < 0 || (max_interfaces > 0 && !out)) return LB_EINVAL;
+    if (!c->stencil_set) return LB_ESTATE;
+    const int maxw = max_interfaces < 256 ? max_interfaces : 256;
+    int *cnt = reinterpret_cast<int *>(obs_results(c) + 8);
+    lb_flat_obs *res = reinterpret_cast<lb_flat_obs *>(obs_results(c) + 16);
+    cudaError_t e = flat_interfaces(c, maxw, res, cnt);
+    if (e == cudaErrorNotSupported) return LB_EUNSUPPORTED;
+    if (e == cudaErrorInvalidValue) return LB_EINVAL;
+    if (e != cudaSuccess) return cuda_fail(e, "flat interface kernels");
+    int k = 0;
+    CK(cudaMemcpyAsync(&k, cnt, sizeof k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int m = k < maxw ? k : maxw;
+    if (m > 0)
+        CK(cudaMemcpyAsync(out, res, (size_t)m * sizeof(lb_flat_obs), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_found) *n_found = k;
+    return LB_OK;
+}
+
+lb_status lb_curved_interface(lb_ctx *c, const double *center, lb_curved_obs *out) {
+    if (!c || !center || !out) return LB_EINVAL;
+    if (!c->stencil_set) return LB_ESTATE;
+    const int ext[3] = {c->g.nx, c->g.ny, c->g.nz};
+    for (int k = 0; k < c->D; ++k)
+        if (!(center[k] >= 0.0 && center[k] < ext[k])) return LB_EINVAL;
+    lb_curved_obs *res = reinterpret_cast<lb_curved_obs *>(obs_results(c) + 16);
+    double cen[3] = {center[0], center[1], c->D == 3 ? center[2] : 0.0};
+    cudaError_t e = curved_interface(c, cen, c->e2, res);
+    if (e == cudaErrorNotSupported) return LB_EUNSUPPORTED;
+    if (e == cudaErrorInvalidValue) return LB_EINVAL;
+    if (e != cudaSuccess) return cuda_fail(e, "curved interface kernels");
+    CK(cudaMemcpyAsync(out, res, sizeof *out, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!(out->n_in != out->n_out)) return LB_EINVAL;   // no interface
+    return LB_OK;
+}
+
+namespace {
+// least-squares line y = a x + b
+bool fit_line(const double *x, const double *y, int n, double *a, double *b) {
+    double sx = 0, sy = 0;
+    for (int i = 0; i < n; ++i) { sx += x[i]; sy += y[i]; }
+    const double mx = sx / n, my = sy / n;
+    double sxx = 0, sxy = 0;
+    for (int i = 0; i < n; ++i) {
+        sxx += (x[i] - mx) * (x[i] - mx);
+        sxy += (x[i] - mx) * (y[i] - my);
+    }
+    if (!(sxx > 0)) return false;
+    *a = sxy / sxx;
+    *b = my - *a * mx;
+    return true;
+}
+}  // namespace
+
+lb_status lb_fit_laplace(const lb_curved_obs *runs, int n, int dim, double *sigma,
+                         double *intercept) {
+    if (!runs || n < 2 || (dim != 2 && dim != 3) || !sigma) return LB_EINVAL;
+    std::vector<double> x(n), y(n);
+    for (int i = 0; i < n; ++i) {
+        const double sg = runs[i].bubble ? -1.0 : 1.0;
+        x[i] = sg / runs[i].R_e;
+        y[i] = sg * runs[i].dP;
+    }
+    double a, b;
+    if (!fit_line(x.data(), y.data(), n, &a, &b)) return LB_EINVAL;
+    *sigma = a / (dim - 1);
+    if (intercept) *intercept = b;
+    return LB_OK;
+}
+
+lb_status lb_fit_tolman(const lb_curved_obs *runs, int n, int dim, double sigma0, double *delta,
+                        double *intercept) {
+    if (!runs || n < 2 || (dim != 2 && dim != 3) || !delta || !(sigma0 != 0.0)) return LB_EINVAL;
+    std::vector<double> x(n), y(n);
+    for (int i = 0; i < n; ++i) {
+        const double sg = runs[i].bubble ? -1.0 : 1.0;
+        x[i] = sg / runs[i].R_s;
+        y[i] = runs[i].dP * runs[i].R_s / ((dim - 1) * sigma0);
+    }
+    double a, b;
+    if (!fit_line(x.data(), y.data(), n, &a, &b)) return LB_EINVAL;
+    *delta = -a / (dim - 1);
+    if (intercept) *intercept = b;
     return LB_OK;
 }
 
@@ -554,10 +628,9 @@ lb_status lb_get_fields(lb_ctx *c, double *rho, double *u) {
     if (!c) return LB_EINVAL;
     if (!c->stencil_set) return LB_ESTATE;
     const long long N = c->g.N;
-    lb_status s = ensure_scratch(c, (size_t)(2 + 2 * c->D) * N * sizeof(double));
-    if (s != LB_OK) return s;
-    double *n = c->dscratch, *ud = n + 2 * N, *mom = ud + c->D * N;
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_fields(c, n, ud, mom) : f32_fields(c, n, ud, mom);
+    if ((size_t)(2 + c->D) * N * sizeof(double) > stage_bytes(c)) return LB_EUNSUPPORTED;
+    double *n = stage_ptr(c), *ud = n + 2 * N;
+    cudaError_t e = c->p.precision == LB_FP64 ? f64_fields(c, n, ud, nullptr) : f32_fields(c, n, ud, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "fields kernels");
     if (rho) CK(cudaMemcpyAsync(rho, n, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (u) CK(cudaMemcpyAsync(u, ud, c->D * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -568,11 +641,16 @@ lb_status lb_get_fields(lb_ctx *c, double *rho, double *u) {
 lb_status lb_get_state(lb_ctx *c, double *f) {
     if (!c || !f) return LB_EINVAL;
     const long long N = c->g.N;
-    lb_status s = ensure_scratch(c, (size_t)c->Q * N * sizeof(double));
-    if (s != LB_OK) return s;
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, c->dscratch) : f32_get_state(c, c->dscratch);
-    if (e != cudaSuccess) return cuda_fail(e, "get_state kernel");
-    CK(cudaMemcpyAsync(f, c->dscratch, (size_t)c->Q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    const int chunk = stage_pops(c);
+    if (chunk < 1) return LB_EUNSUPPORTED;
+    double *st = stage_ptr(c);
+    for (int i0 = 0; i0 < c->Q; i0 += chunk) {
+        const int i1 = i0 + chunk < c->Q ? i0 + chunk : c->Q;
+        cudaError_t e = c->p.precision == LB_FP64 ? f64_get_state(c, st, i0, i1) : f32_get_state(c, st, i0, i1);
+        if (e != cudaSuccess) return cuda_fail(e, "get_state kernel");
+        CK(cudaMemcpyAsync(f + (size_t)i0 * N, st, (size_t)(i1 - i0) * N * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     return LB_OK;
 }
@@ -580,11 +658,20 @@ lb_status lb_get_state(lb_ctx *c, double *f) {
 lb_status lb_set_state(lb_ctx *c, const double *f) {
     if (!c || !f) return LB_EINVAL;
     const long long N = c->g.N;
-    lb_status s = ensure_scratch(c, (size_t)c->Q * N * sizeof(double));
-    if (s != LB_OK) return s;
-    CK(cudaMemcpyAsync(c->dscratch, f, (size_t)c->Q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_set_state(c, c->dscratch) : f32_set_state(c, c->dscratch);
-    if (e != cudaSuccess) return cuda_fail(e, "set_state kernel");
+    const int chunk = stage_pops(c);
+    if (chunk < 1) return LB_EUNSUPPORTED;
+    double *st = stage_ptr(c);
+    for (int i0 = 0; i0 < c->Q; i0 += chunk) {
+        const int i1 = i0 + chunk < c->Q ? i0 + chunk : c->Q;
+        CK(cudaMemcpyAsync(st, f + (size_t)i0 * N, (size_t)(i1 - i0) * N * sizeof(double),
+                           cudaMemcpyHostToDevice, c->stream));
+        cudaError_t e = c->p.precision == LB_FP64 ? f64_set_state(c, st, i0, i1) : f32_set_state(c, st, i0, i1);
+        if (e != cudaSuccess) return cuda_fail(e, "set_state kernel");
+    }
+    if (c->p.precision != LB_FP64) {
+        cudaError_t e = ghosts_refresh(c);
+        if (e != cudaSuccess) return cuda_fail(e, "ghost refresh");
+    }
     CK(cudaStreamSynchronize(c->stream));
     return LB_OK;
 }

@@ -86,29 +86,28 @@ cudaError_t f32_fields(lb_ctx *c, double *n, double *u, double *mom) {
     return cudaGetLastError();
 }
 
-cudaError_t f32_get_state(lb_ctx *c, double *f) {
+cudaError_t f32_get_state(lb_ctx *c, double *f, int i0, int i1) {
     auto k = consts_as<double>(c->k);
     int gb = grid_for(c->g.N);
     const float *A = (const float *)c->f[c->cur];
     if (c->Q == 9)
-        k_get_state<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_get_state<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     else
-        k_get_state<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_get_state<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     c->launches++;
     return cudaGetLastError();
 }
 
-cudaError_t f32_set_state(lb_ctx *c, const double *f) {
+cudaError_t f32_set_state(lb_ctx *c, const double *f, int i0, int i1) {
     auto k = consts_as<double>(c->k);
     int gb = grid_for(c->g.N);
     float *A = (float *)c->f[c->cur];
     if (c->Q == 9)
-        k_set_state<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_set_state<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     else
-        k_set_state<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_set_state<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     c->launches++;
-    cudaError_t e = cudaGetLastError();
-    return e != cudaSuccess ? e : ghosts_refresh(c);
+    return cudaGetLastError();
 }
 
 }  // namespace sclbm

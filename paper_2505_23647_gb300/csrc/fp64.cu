@@ -1,7 +1,7 @@
 // fp64.cu -- binary64 path (compiled with -fmad=false: every product and sum
 // below rounds exactly as written, matching the documented FP64 order), the
-// FP64 reductions for lb_observables, the lattice pressure tensor
-// (Appendices E and F) and the exp diagnostic.
+// link tables of the lattice pressure tensor (Appendices E and F; the tensor
+// itself is in observe.cu) and the exp diagnostic.
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -76,183 +76,31 @@ cudaError_t f64_fields(lb_ctx *c, double *n, double *u, double *mom) {
     return cudaGetLastError();
 }
 
-cudaError_t f64_get_state(lb_ctx *c, double *f) {
+cudaError_t f64_get_state(lb_ctx *c, double *f, int i0, int i1) {
     auto k = consts_as<double>(c->k);
     int gb = grid_for(c->g.N);
     const double *A = (const double *)c->f[c->cur];
     if (c->Q == 9)
-        k_get_state<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_get_state<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     else
-        k_get_state<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_get_state<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     c->launches++;
     return cudaGetLastError();
 }
 
-cudaError_t f64_set_state(lb_ctx *c, const double *f) {
+cudaError_t f64_set_state(lb_ctx *c, const double *f, int i0, int i1) {
     auto k = consts_as<double>(c->k);
     int gb = grid_for(c->g.N);
     double *A = (double *)c->f[c->cur];
     if (c->Q == 9)
-        k_set_state<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_set_state<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     else
-        k_set_state<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k);
+        k_set_state<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, c->g, f, k, i0, i1);
     c->launches++;
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// FP64 reductions: compensated (double-double) sums in a fixed order.
-struct Red {
-    ddv mass, mom[3];
-    double umax2, rmin, rmax;
-};
-
-__device__ __forceinline__ void red_combine(Red &a, const Red &b) {
-    a.mass = dd_add(a.mass, b.mass);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a.mom[k] = dd_add(a.mom[k], b.mom[k]);
-    a.umax2 = fmax(a.umax2, b.umax2);
-    a.rmin = fmin(a.rmin, b.rmin);
-    a.rmax = fmax(a.rmax, b.rmax);
-}
-
-__device__ __forceinline__ Red red_shfl(const Red &r, int off) {
-    Red o;
-    o.mass.hi = __shfl_down_sync(0xffffffffu, r.mass.hi, off);
-    o.mass.lo = __shfl_down_sync(0xffffffffu, r.mass.lo, off);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        o.mom[k].hi = __shfl_down_sync(0xffffffffu, r.mom[k].hi, off);
-        o.mom[k].lo = __shfl_down_sync(0xffffffffu, r.mom[k].lo, off);
-    }
-    o.umax2 = __shfl_down_sync(0xffffffffu, r.umax2, off);
-    o.rmin = __shfl_down_sync(0xffffffffu, r.rmin, off);
-    o.rmax = __shfl_down_sync(0xffffffffu, r.rmax, off);
-    return o;
-}
-
-__device__ __forceinline__ Red red_block(Red r) {
-    __shared__ Red sh[32];
-    for (int off = 16; off > 0; off >>= 1) {
-        Red o = red_shfl(r, off);
-        red_combine(r, o);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = r;
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    if (wid == 0) {
-        if (lane < nw) r = sh[lane];
-        else {
-            r.mass = {0.0, 0.0};
-            for (int k = 0; k < 3; ++k) r.mom[k] = {0.0, 0.0};
-            r.umax2 = 0.0;
-            r.rmin = __longlong_as_double(0x7ff0000000000000ULL);
-            r.rmax = -__longlong_as_double(0x7ff0000000000000ULL);
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            Red o = red_shfl(r, off);
-            red_combine(r, o);
-        }
-    }
-    return r;
-}
-
-__device__ __forceinline__ Red red_zero() {
-    Red r;
-    r.mass = {0.0, 0.0};
-    for (int k = 0; k < 3; ++k) r.mom[k] = {0.0, 0.0};
-    r.umax2 = 0.0;
-    r.rmin = __longlong_as_double(0x7ff0000000000000ULL);
-    r.rmax = -__longlong_as_double(0x7ff0000000000000ULL);
-    return r;
-}
-
-__global__ void __launch_bounds__(256) k_reduce1(long long N, int D, const double *__restrict__ n,
-                                                 const double *__restrict__ u,
-                                                 const double *__restrict__ mom, Red *partial) {
-    Red r = red_zero();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += stride) {
-        const double ns = n[s];
-        r.mass = dd_add(r.mass, dd_two_sum(ns, 0.0));
-        double uu = u[s] * u[s];
-        for (int mu = 0; mu < D; ++mu) {
-            if (mu) uu = uu + u[(long long)mu * N + s] * u[(long long)mu * N + s];
-            r.mom[mu] = dd_add(r.mom[mu], ddv{mom[(long long)mu * N + s], 0.0});
-        }
-        r.umax2 = fmax(r.umax2, uu);
-        r.rmin = fmin(r.rmin, ns);
-        r.rmax = fmax(r.rmax, ns);
-    }
-    r = red_block(r);
-    if (threadIdx.x == 0) partial[blockIdx.x] = r;
-}
-
-__global__ void __launch_bounds__(256) k_reduce2(int nb, const Red *__restrict__ partial,
-                                                 double *out) {
-    Red r = red_zero();
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) red_combine(r, partial[b]);
-    r = red_block(r);
-    if (threadIdx.x == 0) {
-        out[0] = r.mass.hi + r.mass.lo;
-        for (int k = 0; k < 3; ++k) out[1 + k] = r.mom[k].hi + r.mom[k].lo;
-        out[4] = sqrt(r.umax2);
-        out[5] = r.rmin;
-        out[6] = r.rmax;
-    }
-}
-
-cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
-                       double *out_dev) {
-    const int nb = 1024;
-    k_reduce1<<<nb, 256, 0, c->stream>>>(c->g.N, c->D, n, u, mom, (Red *)c->red);
-    k_reduce2<<<1, 256, 0, c->stream>>>(nb, (const Red *)c->red, out_dev);
-    c->launches += 2;
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Lattice pressure tensor.  Per pair e (with -e): the endpoint products
-// A = psi(x) (psi(x+e) + psi(x-e)) and the interior/midpoint link products
-template <int D>
-__global__ void __launch_bounds__(128) k_ptensor(Geom g, const double *__restrict__ n,
-                                                 const double *__restrict__ psi, const PTPairs P,
-                                                 double *__restrict__ out) {
-    constexpr int NC = D == 2 ? 3 : 6;
-    constexpr int cmu[6] = {0, 0, D == 2 ? 1 : 0, 1, 1, 2};
-    constexpr int cnu[6] = {0, 1, D == 2 ? 1 : 2, 1, 2, 2};
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
-        int x, y, z;
-        coords(g, s, x, y, z);
-        double Ps[NC];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) Ps[k] = (cmu[k] == cnu[k]) ? n[s] / 3.0 : 0.0;
-        const double p0 = psi[s];
-        for (int a = 0; a < P.npairs; ++a) {
-            const int e0 = P.v[a][0], e1 = P.v[a][1], e2 = P.v[a][2];
-            const double A = p0 * (psi[site(g, x + e0, y + e1, z + e2)] +
-                                   psi[site(g, x - e0, y - e1, z - e2)]);
-            double B = 0.0;
-            for (int l = 0; l < P.nlink[a]; ++l) {
-                const signed char *q = &P.link[a][l][0][0];
-                B = B + psi[site(g, x + q[0], y + q[1], z + q[2])] *
-                            psi[site(g, x + q[3], y + q[4], z + q[5])];
-            }
-            const double sc = P.w[a] * (P.kA[a] * A + P.kB[a] * B);
-            const int e[3] = {e0, e1, e2};
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const int ee = e[cmu[k]] * e[cnu[k]];
-                if (ee) Ps[k] = Ps[k] + sc * (double)ee;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NC; ++k) out[(long long)k * g.N + s] = Ps[k];
-    }
-}
-
 static int igcd(int a, int b) {
     a = a < 0 ? -a : a;
     b = b < 0 ? -b : b;
@@ -315,18 +163,6 @@ bool build_pt_pairs(const lb_ctx *c, PTPairs *P) {
         }
     }
     return true;
-}
-
-cudaError_t ptensor(lb_ctx *c, const double *n, const double *psi, double *out) {
-    static PTPairs P;   // host staging (large); calls on one context are serialised
-    if (!build_pt_pairs(c, &P)) return cudaErrorNotSupported;
-    int gb = grid_for(c->g.N, 128);
-    if (c->D == 2)
-        k_ptensor<2><<<gb, 128, 0, c->stream>>>(c->g, n, psi, P, out);
-    else
-        k_ptensor<3><<<gb, 128, 0, c->stream>>>(c->g, n, psi, P, out);
-    c->launches++;
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

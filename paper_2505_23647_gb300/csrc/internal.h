@@ -131,6 +131,7 @@ struct lb_ctx {
     sclbm::PairsF64 pairs64;
     sclbm::PairsF32 pairs32;
     int n_groups;
+    double e2;                // second moment of the stencil (lb_stencil_info.e2)
     int group_base[LB_MAX_PAIRS][3];
     double group_w[LB_MAX_PAIRS];
     bool stencil_set;
@@ -149,9 +150,7 @@ struct lb_ctx {
     void *f[2];               // population buffers [Q][N] (post-collision, pre-stream)
     int cur;                  // buffer holding the current state
     void *psi;                // [N] psi of the precision in use
-    double *dscratch;         // on-demand binary64 scratch
-    size_t dscratch_bytes;
-    double *red;              // reduction partials
+    double *red;              // reduction partials and small results (128 KB)
     sclbm::Flags *flags;      // device counters
     cudaStream_t stream;
     bool own_stream;
@@ -180,15 +179,15 @@ cudaError_t f64_init(lb_ctx *c, const double *rho, const double *u);
 cudaError_t f64_step(lb_ctx *c);          // one step, swaps buffers
 cudaError_t f64_psi(lb_ctx *c);           // psi of current state into c->psi
 cudaError_t f64_fields(lb_ctx *c, double *n, double *u, double *mom);
-cudaError_t f64_get_state(lb_ctx *c, double *f);
-cudaError_t f64_set_state(lb_ctx *c, const double *f);
+cudaError_t f64_get_state(lb_ctx *c, double *f, int i0, int i1);   // populations [i0, i1)
+cudaError_t f64_set_state(lb_ctx *c, const double *f, int i0, int i1);
 cudaError_t f64_density_psi(lb_ctx *c, double *n, double *psi);
 cudaError_t f32_init(lb_ctx *c, const double *rho, const double *u);
 cudaError_t f32_step(lb_ctx *c);
 cudaError_t f32_psi(lb_ctx *c);
 cudaError_t f32_fields(lb_ctx *c, double *n, double *u, double *mom);
-cudaError_t f32_get_state(lb_ctx *c, double *f);
-cudaError_t f32_set_state(lb_ctx *c, const double *f);
+cudaError_t f32_get_state(lb_ctx *c, double *f, int i0, int i1);
+cudaError_t f32_set_state(lb_ctx *c, const double *f, int i0, int i1);   // no ghost refresh
 cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi);
 // fused single-pass D3Q19 step (fused3d.cu)
 bool fused3d_applicable(const lb_ctx *c, float *W, int *ng);
@@ -199,10 +198,17 @@ bool tma_make_maps(lb_ctx *c);
 bool fused2d_applicable(const lb_ctx *c, float *W5);
 cudaError_t f32_fused2d_step(lb_ctx *c);
 cudaError_t ghosts_refresh(lb_ctx *c);   // padded layouts: refresh ghost cells of f[cur]
-// precision-independent (fp64.cu): reductions, pressure tensor, exp diagnostic
-cudaError_t obs_reduce(lb_ctx *c, const double *n, const double *u, const double *mom,
-                       double *out_host9);
-cudaError_t ptensor(lb_ctx *c, const double *n, const double *psi, double *out);
+// observe.cu: what is measured on a lattice, all staged without allocation
+// in the idle population buffer (stage_ptr, stage_bytes bytes) and the
+// context's reduction buffer
+size_t stage_bytes(const lb_ctx *c);
+double *stage_ptr(lb_ctx *c);
+cudaError_t obs_fused(lb_ctx *c);          // 7 results at obs_results(c)
+double *obs_results(lb_ctx *c);
+void psi64_field(lb_ctx *c, double *psi);  // binary64 psi of every node
+cudaError_t ptensor_field(lb_ctx *c, double *psi, double *out);
+cudaError_t flat_interfaces(lb_ctx *c, int maxw, lb_flat_obs *out_dev, int *count_dev);
+cudaError_t curved_interface(lb_ctx *c, const double *center, double e2, lb_curved_obs *out_dev);
 // lattice pressure tensor of Appendices E/F, per pair (e, -e): A = psi(x) (psi(x+e) +
 // psi(x-e)), B = sum over the pair's links of psi(x+a) psi(x+b) (links prepared
 // on the host), s = W (kA A + kB B), P^{mu nu}(x) += s e^mu e^nu, from (n/3) delta

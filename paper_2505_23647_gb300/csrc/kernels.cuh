@@ -310,7 +310,7 @@ __global__ void k_fields64(const T *__restrict__ A, Geom g, const PairsF64 P, Co
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) {
             u_out[(long long)mu * g.N + s] = u[mu];
-            mom_out[(long long)mu * g.N + s] = m[mu];
+            if (mom_out) mom_out[(long long)mu * g.N + s] = m[mu];
         }
     }
 }
@@ -345,31 +345,33 @@ __global__ void k_init(T *__restrict__ A, Geom g, const double *__restrict__ rho
 
 template <typename T, int D, int Q, bool SHIFT>
 __global__ void k_get_state(const T *__restrict__ A, Geom g, double *__restrict__ out,
-                            ConstsT<double> k) {
+                            ConstsT<double> k, int i0, int i1) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
         int x, y, z;
         coords(g, s, x, y, z);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
+            if (i < i0 || i >= i1) continue;
             double v = (double)A[(long long)i * g.Np +
                                  popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))];
             if (SHIFT) v = v + k.w[i] * k.rho0;
-            out[(long long)i * g.N + s] = v;
+            out[(long long)(i - i0) * g.N + s] = v;
         }
     }
 }
 
 template <typename T, int D, int Q, bool SHIFT>
 __global__ void k_set_state(T *__restrict__ A, Geom g, const double *__restrict__ in,
-                            ConstsT<double> k) {
+                            ConstsT<double> k, int i0, int i1) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
         int x, y, z;
         coords(g, s, x, y, z);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            double v = in[(long long)i * g.N + s];
+            if (i < i0 || i >= i1) continue;
+            double v = in[(long long)(i - i0) * g.N + s];
             if (SHIFT) v = v - k.w[i] * k.rho0;
             A[(long long)i * g.Np +
               popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)v;

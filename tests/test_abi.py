@@ -97,3 +97,29 @@ def test_nonpositive_density_rejected_on_host(P):
     with pytest.raises(P.LbError) as ei:
         P.lb_create(p, rho)
     assert ei.value.status == P.LB_EINVAL
+
+
+def test_laplace_and_tolman_fits_match_the_oracle_fits(P):
+    """lb_fit_laplace / lb_fit_tolman are host arithmetic: the same lines as
+    the oracle's laplace_sigma / tolman_curved_fit on made-up results."""
+    from oracle import analysis as A
+    rng = np.random.default_rng(7)
+    runs = []
+    for R in (8.0, 11.0, 15.0, 22.0):
+        for b in (False, True):
+            Re = R * (1 + 0.01 * rng.standard_normal())
+            Rs = Re - (0.8 if not b else -0.5)
+            dP = 0.18 / Re * (1 + 0.05 * rng.standard_normal())
+            runs.append({"n_in": 0.3 if b else 3.8, "n_out": 3.8 if b else 0.3, "P_in": 0.1 + dP,
+                         "P_out": 0.1, "dP": dP, "R_e": Re, "R_s": Rs, "sigma_s": dP * Rs,
+                         "bubble": b})
+    s, i = P.lb_fit_laplace(runs, 2)
+    s0, i0 = A.laplace_sigma(runs, 2)
+    assert s == pytest.approx(s0, rel=1e-12) and i == pytest.approx(i0, rel=1e-9, abs=1e-15)
+    d, j = P.lb_fit_tolman(runs, 2, 0.18)
+    d0, j0 = A.tolman_curved_fit(runs, 0.18, 2)
+    assert d == pytest.approx(d0, rel=1e-12) and j == pytest.approx(j0, rel=1e-12)
+    s3, _ = P.lb_fit_laplace(runs, 3)
+    assert s3 == pytest.approx(s0 / 2, rel=1e-12)
+    with pytest.raises(P.LbError):
+        P.lb_fit_laplace(runs[:1], 2)
