@@ -225,6 +225,153 @@ def run_reference(args, dist, rank, ws):
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+# ---------------------------------------------------------------------------
+# Configurations as written: C1 (the 256 x 4 binary64 slab) and C2 (the 20
+# droplet / bubble runs), each with the coupling read literally (G' = G =
+# -5, the library's default), read with c_s^2 (G' = -5/3, the printed eq.
+# sc_f) and, as a stable two-phase companion, G' = -3 from its coexistence
+# densities (eq. SCMaxwell).  Physics from the library's own binary64
+# interface observables (lb_flat_interfaces, lb_curved_interface, fits).
+COEX_GP3 = (0.4558015024901948, 2.249571904134268)   # eq. SCMaxwell at G' = -3
+
+
+def _slab_rho(L, nx, ny, n_gas, n_liq):
+    return L.tanh_slab(nx, ny, 1, 64 * nx // 256, 192 * nx // 256, n_gas, n_liq, 2.0)
+
+
+def c1_leg(P, L, stream, steps=10000):
+    """C1: D2Q9 E4 binary64, tau = 1, periodic 256 x 4, liquid slab x in
+    [64, 192) with rho = 0.15 + 1.75 (tanh((x-64)/2) - tanh((x-192)/2))/2,
+    10,000 steps: per reading, stability (or the first failing step), mass
+    drift, and for a two-phase state the coexistence densities, sigma_0 and
+    the Tolman length of both interfaces."""
+    import torch
+    out = {"lattice": "D2Q9 E4 256x4 binary64, tau 1", "steps": steps}
+    readings = [("literal_G-5", -5.0, "literal", (0.15, 1.9)),
+                ("cs2_G-5", -5.0, "paper", (0.15, 1.9)),
+                ("companion_Gp-3", -3.0, "literal", COEX_GP3)]
+    for name, G_, conv, (ng, nl) in readings:
+        rho = _slab_rho(L, 256, 4, ng, nl)
+        lat = P.Lattice("D2Q9", (256, 4), rho, L.E4_2D.bases, L.E4_2D.weights, precision="fp64",
+                        tau=1.0, G=G_, convention=conv, stream=stream.cuda_stream)
+        m0 = lat.observables()["mass"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ob = lat.observables()
+        r = {"G": G_, "G_prime": G_ / 3.0 if conv == "paper" else G_, "initial": [ng, nl],
+             "stable": ob["status"] == P.LB_OK, "first_failing_step": ob["error_step"],
+             "steps_per_s": steps / (ms * 1e-3), "rho_min": ob["rho_min"], "rho_max": ob["rho_max"]}
+        if r["stable"]:
+            r["mass_drift_rel"] = (ob["mass"] - m0) / m0
+            ifs = lat.flat_interfaces()
+            r["interfaces"] = len(ifs)
+            if ifs:
+                r["n_l"] = [i["n_l"] for i in ifs]
+                r["n_g"] = [i["n_g"] for i in ifs]
+                r["sigma0"] = [i["sigma"] for i in ifs]
+                r["delta"] = [i["delta"] for i in ifs]
+                r["delta_ads"] = [i["delta_ads"] for i in ifs]
+        lat.close()
+        out[name] = r
+    return out
+
+
+def c2_leg(P, L, stream, steps=40000):
+    """C2: D2Q9 E8 (24 vectors), 10 droplets and 10 bubbles, R = 8 .. 48 in
+    periodic 256 x 256 boxes, tanh width 2, 40,000 steps, shifted binary32
+    (one batch) and binary64 (each lattice on its own stream): per run
+    stability, R_e, R_s, sigma_s, Delta P; the Laplace sigma and the curved
+    Tolman length over the stable runs, and their binary32-vs-binary64
+    relative differences.  sigma_0 for the Tolman fit: a 256 x 4 binary64
+    slab of the same model."""
+    import torch
+    radii = (8, 12, 16, 20, 24, 28, 32, 36, 40, 48)
+    c = (128.0, 128.0)
+    out = {"lattice": "D2Q9 E8 256x256, tau 1", "steps": steps, "radii": list(radii)}
+    readings = [("literal_G-5", -5.0, "literal", (0.15, 1.9)),
+                ("companion_Gp-3", -3.0, "literal", COEX_GP3)]
+    for name, G_, conv, (ng, nl) in readings:
+        rhos = [L.tanh_sphere(256, 256, 1, R, nl, ng, 2.0, center=(c[0], c[1], 0.0)) for R in radii] + \
+               [L.tanh_sphere(256, 256, 1, R, ng, nl, 2.0, center=(c[0], c[1], 0.0)) for R in radii]
+        res = {}
+        t0 = time.perf_counter()
+        for prec in ("fp32", "fp64"):
+            if prec == "fp32":
+                lats = [P.Lattice("D2Q9", (256, 256), r, L.E8_2D.bases, L.E8_2D.weights,
+                                  precision="fp32", tau=1.0, G=G_, convention=conv,
+                                  stream=stream.cuda_stream) for r in rhos]
+                b = P.Batch(lats, stream=stream.cuda_stream)
+                b.step(steps)
+                b.sync()
+                b.close()
+            else:
+                lats = [P.Lattice("D2Q9", (256, 256), r, L.E8_2D.bases, L.E8_2D.weights,
+                                  precision="fp64", tau=1.0, G=G_, convention=conv) for r in rhos]
+                for _ in range(steps // 1000):
+                    for lat in lats:
+                        lat.step(1000)
+            torch.cuda.synchronize()
+            runs = []
+            for lat in lats:
+                ob = lat.observables()
+                r = {"stable": ob["status"] == P.LB_OK, "first_failing_step": ob["error_step"],
+                     "rho_min": ob["rho_min"], "rho_max": ob["rho_max"]}
+                if r["stable"]:
+                    try:
+                        r.update(lat.curved_interface(c))
+                    except P.LbError:
+                        r["interface"] = False
+                runs.append(r)
+                lat.close()
+            res[prec] = runs
+        fin = lambda x: x["stable"] and all(k in x and np.isfinite(x[k]) and x[k] > 0
+                                             for k in ("R_e", "R_s", "dP"))
+        ok = [i for i in range(20) if all(fin(res[p][i]) for p in res)]
+        # sigma_0 of the same model: a flat 256 x 4 binary64 slab
+        sig0 = None
+        try:
+            sl = P.Lattice("D2Q9", (256, 4), _slab_rho(L, 256, 4, ng, nl), L.E8_2D.bases,
+                           L.E8_2D.weights, precision="fp64", tau=1.0, G=G_, convention=conv,
+                           stream=stream.cuda_stream)
+            sl.step(10000)
+            if sl.observables()["status"] == P.LB_OK:
+                ifs = sl.flat_interfaces()
+                if ifs:
+                    sig0 = float(np.mean([i["sigma"] for i in ifs]))
+            sl.close()
+        except P.LbError:
+            pass
+        r = {"G": G_, "initial": [ng, nl], "stable_runs": {p: sum(x["stable"] for x in res[p]) for p in res},
+             "first_failing_steps": {p: [x["first_failing_step"] for x in res[p]] for p in res},
+             "seconds": time.perf_counter() - t0, "sigma0_flat": sig0}
+        if len(ok) >= 2:
+            fits = {}
+            for p in res:
+                sel = [res[p][i] for i in ok]
+                try:
+                    fits[p] = {"laplace_sigma": P.lb_fit_laplace(sel, 2)[0]}
+                    if sig0:
+                        fits[p]["tolman_delta"] = P.lb_fit_tolman(sel, 2, sig0)[0]
+                except P.LbError:
+                    fits[p] = {}
+            r["fits"] = fits
+            rel = lambda a, b: abs(a - b) / abs(b)
+            r["fp32_vs_fp64_rel"] = {k: rel(fits["fp32"][k], fits["fp64"][k]) for k in fits["fp64"]
+                                     if k in fits["fp32"]}
+            r["fp32_vs_fp64_rel"]["R_s_max"] = max(rel(res["fp32"][i]["R_s"], res["fp64"][i]["R_s"]) for i in ok)
+            r["fp32_vs_fp64_rel"]["sigma_s_max"] = max(rel(res["fp32"][i]["sigma_s"], res["fp64"][i]["sigma_s"]) for i in ok)
+            r["runs_fp64"] = [{k: res["fp64"][i][k] for k in ("bubble", "R_e", "R_s", "sigma_s", "dP")}
+                              for i in ok]
+        r["runs_with_interface"] = len(ok)
+        out[name] = r
+    return out
+
+
 def run_gb300(args, dist, rank, ws):
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -562,6 +709,11 @@ def run_gb300(args, dist, rank, ws):
                "d2h_bytes_per_step": (N * 8 + 88) / args.steps,
                "seconds": dt, "mass": o2["mass"]}
 
+    c1 = c2 = None
+    if not args.no_configs:
+        c1 = c1_leg(P, L, stream)
+        c2 = c2_leg(P, L, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         sub, csteps = 64, 12
@@ -585,7 +737,7 @@ def run_gb300(args, dist, rank, ws):
             "f2_forcing": f2,
             "fused_kernel": fused,
             "batched_2d": batched, "adjoint": adjoint, "slab_fp64": slab,
-            "droplets_2d": drops,
+            "droplets_2d": drops, "c1": c1, "c2": c2,
             "observables": {"mass": obs["mass"], "umax": obs["umax"],
                             "rho_min": obs["rho_min"], "rho_max": obs["rho_max"],
                             "stable": stable, "first_unstable_step": obs["error_step"]},
@@ -609,6 +761,8 @@ def main():
     ap.add_argument("--no-droplets", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the C1 / C2 runs as written (physics, ~1 min)")
     ap.add_argument("--zchunk", type=int, default=0,
                     help="z planes per CTA of the fused kernel (default: the library's)")
     ap.add_argument("--size", type=int, default=256,

@@ -446,6 +446,45 @@ lb_status lb_destroy(lb_ctx *c) {
     return LB_OK;
 }
 
+namespace {
+
+// steps per replay of a context's CUDA graph (even: the buffer parity
+// returns to where it started)
+constexpr int kStepGraph = 32;
+
+cudaError_t one_step(lb_ctx *c) { return c->p.precision == LB_FP64 ? f64_step(c) : f32_step(c); }
+
+void drop_graph(lb_ctx *c) {
+    if (c->graph_valid) cudaGraphExecDestroy(c->graph);
+    c->graph_valid = false;
+}
+
+// Capture kStepGraph steps of the context's stream into c->graph (nothing
+// runs during the capture; the host-side buffer parity and launch count are
+// restored).
+lb_status build_step_graph(lb_ctx *c) {
+    drop_graph(c);
+    const int cur0 = c->cur;
+    const long long l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "step graph capture");
+    for (int t = 0; t < kStepGraph && e == cudaSuccess; ++t) e = one_step(c);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    c->graph_launches = c->launches - l0;
+    c->launches = l0;
+    c->cur = cur0;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "step graph");
+    c->graph_valid = true;
+    c->graph_cur = cur0;
+    return LB_OK;
+}
+
+}  // namespace
+
 lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const double *W,
                          lb_stencil_info *info) {
     if (!c) return LB_EINVAL;
@@ -474,10 +513,7 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
     c->stencil_set = true;
     c->fast3d_ok = fused3d_applicable(c, c->fused_W, &c->fused_ng);
     c->fast2d_ok = fused2d_applicable(c, c->fused2d_W);
-    if (c->graph_valid) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph_valid = false;
-    }
+    drop_graph(c);
     if (info) *info = tmp;
     return LB_OK;
 }
@@ -485,8 +521,32 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
 lb_status lb_step(lb_ctx *c, int nsteps) {
     if (!c || nsteps < 0) return LB_EINVAL;
     if (!c->stencil_set) return LB_ESTATE;
-    for (int t = 0; t < nsteps; ++t) {
-        cudaError_t e = c->p.precision == LB_FP64 ? f64_step(c) : f32_step(c);
+    int t = 0;
+    // long runs replay a captured graph of kStepGraph steps (not while
+    // per-kernel timing records events); the steps before the first replay
+    // run directly, so every kernel has been launched once before a capture
+    if (nsteps >= 3 * kStepGraph && !c->timing) {
+        for (; t < 2; ++t) {
+            cudaError_t e = one_step(c);
+            if (e != cudaSuccess) return cuda_fail(e, "step kernels");
+        }
+        if (c->graph_valid && c->graph_cur != c->cur) {
+            cudaError_t e = one_step(c);
+            if (e != cudaSuccess) return cuda_fail(e, "step kernels");
+            ++t;
+        }
+        if (!c->graph_valid) {
+            lb_status s = build_step_graph(c);
+            if (s != LB_OK) return s;
+        }
+        for (; nsteps - t >= kStepGraph; t += kStepGraph) {
+            cudaError_t e = cudaGraphLaunch(c->graph, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "step graph launch");
+            c->launches += c->graph_launches;
+        }
+    }
+    for (; t < nsteps; ++t) {
+        cudaError_t e = one_step(c);
         if (e != cudaSuccess) return cuda_fail(e, "step kernels");
     }
     c->steps += nsteps;
@@ -737,6 +797,7 @@ lb_status lb_device_counters(lb_ctx *c, long long out[5]) {
 
 lb_status lb_set_option(lb_ctx *c, int option, long long value) {
     if (!c) return LB_EINVAL;
+    drop_graph(c);   // the captured steps bake the options in
     switch (option) {
         case LB_OPT_FUSED:
             c->fused_enabled = value != 0;

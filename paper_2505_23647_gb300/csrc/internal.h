@@ -154,8 +154,10 @@ struct lb_ctx {
     sclbm::Flags *flags;      // device counters
     cudaStream_t stream;
     bool own_stream;
-    cudaGraphExec_t graph;    // two steps, captured on first use
+    cudaGraphExec_t graph;    // kStepGraph steps, captured on first long lb_step
     bool graph_valid;
+    int graph_cur;            // buffer parity the graph starts (and ends) on
+    long long graph_launches; // kernels one replay launches
     long long steps;          // host-side step count
     long long launches;       // kernels launched
     // per-kernel timing (lb_timing)
