@@ -14,12 +14,13 @@
 // march; plane z - R is collided as soon as plane z has been added, from the
 // populations held since then.
 //
-// Layout: the population arrays carry periodic ghost columns (4 on each side
-// in x) and rows (3 on each side in y) around every x-y plane, so the box a
-// tile needs never wraps; the kernel writes a boundary node's values into its
+// Layout: the population arrays carry periodic ghost columns (images of the
+// 4 columns next to each x edge; the interior starts 32 columns into a row
+// so that a warp's row of 32 nodes is one 128-byte line) and rows (3 on each
+// side in y) around every x-y plane, so the box a tile needs never wraps; the kernel writes a boundary node's values into its
 // ghost images as well (fc::store19).  Population i of plane zz is read from
 // A_i(x - xi_i): the box of A_i at plane zz - c_z covering rows
-// y0 - R - c_y .. y0 + TY + R - c_y and columns x0 - 4 .. x0 + 36 (16-byte
+// y0 - R - c_y .. y0 + TY + R - c_y and columns x0 - 4 .. x0 + 35 (16-byte
 // aligned start); the pull's x/y shift becomes a compile-time offset when the
 // box is read.  Requires nx % 32 == 0, ny % 8 == 0.
 //

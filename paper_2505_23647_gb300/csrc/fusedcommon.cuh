@@ -245,6 +245,9 @@ __device__ __forceinline__ void collide19(const float *g, float dn, const float 
 #undef SCLBM_PAIR
 }
 
+// columns next to each x edge whose periodic images a plane box reads
+constexpr int GHOST_X = 4;
+
 // Write a node's 19 post-collision populations; on a padded layout also its
 // periodic images in the ghost columns (x < 4, x >= nx-4) and rows (y < 3,
 // y >= ny-3), so the next step's plane boxes read valid neighbours.
@@ -254,7 +257,7 @@ __device__ __forceinline__ void store19(float *__restrict__ B, const Params &p, 
 #pragma unroll
     for (int i = 0; i < 19; ++i) B[i * p.Np + base] = out[i];
     if (p.ox == 0 && p.oy == 0) return;
-    const int gx = x < p.ox ? x + p.nx : (x >= p.nx - p.ox ? x - p.nx : INT_MIN);
+    const int gx = x < GHOST_X ? x + p.nx : (x >= p.nx - GHOST_X ? x - p.nx : INT_MIN);
     const int gy = y < p.oy ? y + p.ny : (y >= p.ny - p.oy ? y - p.ny : INT_MIN);
     if (gx == INT_MIN && gy == INT_MIN) return;
     const int zb = z * p.pplane;
