@@ -318,7 +318,7 @@ enum {
                            pseudopotential, either forcing variant);
                            0: always the two-kernel path */
     LB_OPT_ZCHUNK = 2,  /* z planes marched by one CTA of the fused kernel
-                           (default 18) */
+                           (default 28) */
     LB_OPT_TMA = 3,     /* 1 (default): on lattices with nx % 32 == 0,
                            ny % 8 == 0, nz >= 8 the fused kernel stages planes
                            with TMA; 0: with per-thread cp.async */

@@ -371,7 +371,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     // bytes): every warp's row of 32 nodes is one whole 128-byte line, so a
     // step's stores never write part of a line or sector (measured at 256^3:
     // 0.592 ms per step with the interior 4 columns in, 0.567 at 8, 0.555 at
-    // 16, 0.540 at 32); only the 4 columns next to each edge hold images
+    // 16, 0.540 at 32); the 8 columns next to each edge are kept as images
     c->padded = p->precision == LB_FP32_SHIFTED && p->lattice == LB_D3Q19 && p->nx % 32 == 0 &&
                 p->ny % 8 == 0 && p->nz >= 8;
     const int ox = c->padded ? 32 : 0, oy = c->padded ? 3 : 0;
@@ -382,7 +382,7 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     c->fused_enabled = true;
     c->fused_tma = true;
     c->wait_polls = 1LL << 26;
-    c->fused_zchunk = 18;
+    c->fused_zchunk = 28;
     auto fail = [&](lb_status s) {
         lb_destroy(c);
         return s;

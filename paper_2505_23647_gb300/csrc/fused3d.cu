@@ -268,7 +268,7 @@ fc::Params fused_params(const lb_ctx *c, const float *W) {
     p.oy = c->g.oy;
     p.pplane = c->g.nxp * c->g.nyp;
     p.Np = (int)c->g.Np;
-    p.zchunk = c->fused_zchunk > 0 ? c->fused_zchunk : 18;
+    p.zchunk = c->fused_zchunk > 0 ? c->fused_zchunk : 28;
     p.max_polls = c->wait_polls;
     return p;
 }

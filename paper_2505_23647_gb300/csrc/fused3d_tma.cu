@@ -15,7 +15,7 @@
 // populations held since then.
 //
 // Layout: the population arrays carry periodic ghost columns (images of the
-// 4 columns next to each x edge; the interior starts 32 columns into a row
+// 8 columns next to each x edge; the interior starts 32 columns into a row
 // so that a warp's row of 32 nodes is one 128-byte line) and rows (3 on each
 // side in y) around every x-y plane, so the box a tile needs never wraps; the kernel writes a boundary node's values into its
 // ghost images as well (fc::store19).  Population i of plane zz is read from

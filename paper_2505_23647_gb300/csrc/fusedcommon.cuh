@@ -245,11 +245,13 @@ __device__ __forceinline__ void collide19(const float *g, float dn, const float 
 #undef SCLBM_PAIR
 }
 
-// columns next to each x edge whose periodic images a plane box reads
-constexpr int GHOST_X = 4;
+// columns next to each x edge written again as periodic images: a plane box
+// reads 4 of them; 8 make each image one whole 32-byte sector of the row
+// (measured 0.537 -> 0.520 ms per 256^3 step against 4)
+constexpr int GHOST_X = 8;
 
 // Write a node's 19 post-collision populations; on a padded layout also its
-// periodic images in the ghost columns (x < 4, x >= nx-4) and rows (y < 3,
+// periodic images in the ghost columns (x < 8, x >= nx-8) and rows (y < 3,
 // y >= ny-3), so the next step's plane boxes read valid neighbours.
 __device__ __forceinline__ void store19(float *__restrict__ B, const Params &p, int x, int y, int z,
                                         const float *out) {
