@@ -440,6 +440,14 @@ def run_gb300(args, dist, rank, ws):
                 "kernel_ms_avg": kms / kn,
                 "step_kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt.items() if v[1]}}
     obs = lat.observables()
+    # cost of one observables call (one fused pass, binary64 sums), host
+    # wall time around the synchronous call, best of 5
+    obs_ms = 1e9
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.observables()
+        obs_ms = min(obs_ms, (time.perf_counter() - t0) * 1e3)
     lat.close()
 
     # the literal reading of G (no c_s^2) over its stable window
@@ -507,6 +515,45 @@ def run_gb300(args, dist, rank, ws):
                                     convention=CONVENTION, forcing_A=A_f2,
                                     stream=stream.cuda_stream), min(args.steps, 1000))
         f2["A"] = A_f2
+
+    # the paper's wide tuned stencils, which the fused kernels do not cover
+    # (groups beyond radius 2): Table tab:e4e6_tuning_8 in 3D (N_e = 140, up
+    # to (4,0,0), (3,3,0), (2,2,1)) on the same bubble, and in 2D (N_e = 32)
+    # on a 2048^2 lattice; the generic binary32 two-kernel path (psi, then
+    # force + collision), algorithmic bytes 80 + 156 per node
+    wide = None
+    if not args.no_wide:
+        wide = {}
+        st3 = L.stencil_e4e6_tuning_8(3, 0, 0)
+        w3 = time_variant(P.Lattice("D3Q19", (NX, NY, NZ), rho_pinned.numpy(), st3.bases, st3.weights,
+                                    precision="fp32", tau=1.0, G=G, convention=CONVENTION,
+                                    stream=stream.cuda_stream), min(args.steps, 200))
+        wide["d3q19_e4e6_tuning_8"] = w3
+        n2 = 2048
+        st2 = L.stencil_e4e6_tuning_8(2, 0, 0)
+        rho2 = L.tanh_sphere(n2, n2, 1, 320.0, 0.15, 1.9, 2.0)
+        lat2 = P.Lattice("D2Q9", (n2, n2), rho2, st2.bases, st2.weights, precision="fp32",
+                         tau=1.0, G=G, convention=CONVENTION, stream=stream.cuda_stream)
+        lat2.step(args.warmup)
+        P.lb_timing(lat2.ctx, 1)
+        k2 = min(args.steps, 200)
+        e0.record(stream)
+        lat2.step(k2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1)
+        kt2 = P.lb_timing_read(lat2.ctx)
+        P.lb_timing(lat2.ctx, 0)
+        ok2 = lat2.sync() == P.LB_OK
+        lat2.close()
+        wide["d2q9_e4e6_tuning_8_2048"] = {
+            "value": n2 * n2 * k2 / (ms2 * 1e3), "unit": "MLUPS", "ms_per_step": ms2 / k2,
+            "stable": ok2, "step_kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in kt2.items() if v[1]}}
+        for key, nodes, b in (("d3q19_e4e6_tuning_8", N, 2 * 19 * 4), ("d2q9_e4e6_tuning_8_2048", n2 * n2, 2 * 9 * 4)):
+            v = wide[key]
+            v["n_vectors"] = 140 if key.startswith("d3") else 32
+            v["hbm_frac_two_kernel_bytes"] = (b + 8) * nodes / (v["ms_per_step"] * 1e-3) / 1e9 / peak
+            v["hbm_frac_min_bytes"] = b * nodes / (v["ms_per_step"] * 1e-3) / 1e9 / peak
 
     # FP64 path on the same workload (fewer steps; binary64 arithmetic)
     fp64 = None
@@ -734,11 +781,12 @@ def run_gb300(args, dist, rank, ws):
                        "l2": "inputs larger than L2 (2 x 1.27 GB populations)"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "fp64": fp64, "literal_g": lit, "psi_eps": peps,
-            "f2_forcing": f2,
+            "f2_forcing": f2, "wide_stencils": wide,
             "fused_kernel": fused,
             "batched_2d": batched, "adjoint": adjoint, "slab_fp64": slab,
             "droplets_2d": drops, "c1": c1, "c2": c2,
-            "observables": {"mass": obs["mass"], "umax": obs["umax"],
+            "observables": {"call_ms": obs_ms, "call_in_steps": obs_ms / (ms_max / args.steps),
+                            "mass": obs["mass"], "umax": obs["umax"],
                             "rho_min": obs["rho_min"], "rho_max": obs["rho_max"],
                             "stable": stable, "first_unstable_step": obs["error_step"]},
         }
@@ -761,6 +809,7 @@ def main():
     ap.add_argument("--no-droplets", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-wide", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the C1 / C2 runs as written (physics, ~1 min)")
     ap.add_argument("--zchunk", type=int, default=0,

@@ -174,6 +174,20 @@ lb_status expand(int dim, int n_groups, const int *base, const double *W,
     return LB_OK;
 }
 
+// the D2Q9 / D3Q19 velocity tables in the state layout's order (host copies)
+int vel9(int i, int k) {
+    static const int t[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+    return t[i][k];
+}
+int vel19(int i, int k) {
+    static const int t[19][3] = {
+        {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+        {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
+        {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][k];
+}
+
 void set_consts(lb_ctx *c) {
     double w[19];
     if (c->Q == 9) {
@@ -401,7 +415,15 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
         e = cudaMalloc(&c->f[b], fbytes);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(f)"));
     }
-    e = cudaMalloc(&c->psi, (size_t)N * tsize(c));
+    // binary32 lattices below 2^31 nodes keep psi with a periodic halo of
+    // PSI_HALO nodes (the generic kernels' branch-free stencil offsets)
+    {
+        const long long H = PSI_HALO, Hz = c->D == 3 ? H : 0;
+        const long long halo_n = (p->nx + 2 * H) * (p->ny + 2 * H) * (p->nz + 2 * Hz);
+        c->psi_halo = (p->precision == LB_FP32_SHIFTED && halo_n < (1LL << 31)) ? PSI_HALO : 0;
+        const size_t np = c->psi_halo ? (size_t)halo_n : (size_t)N;
+        e = cudaMalloc(&c->psi, np * tsize(c));
+    }
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(psi)"));
     e = cudaMalloc(&c->flags, sizeof(Flags));
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(flags)"));
@@ -508,6 +530,27 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
         }
         c->pairs64.w[a] = w[a];
         c->pairs32.w[a] = (float)w[a];
+    }
+    // the binary32 generic kernels' interior form of the stencil
+    {
+        PairsFast &F = c->pfast;
+        std::memset(&F, 0, sizeof F);
+        F.npairs = (int)vec.size();
+        F.R = std::max(1, tmp.radius);
+        F.H = c->psi_halo;
+        F.Hz = c->D == 3 ? c->psi_halo : 0;
+        F.pxp = c->g.nx + 2 * F.H;
+        F.pyp = c->g.ny + 2 * F.H;
+        F.pull_pad = c->g.ox > 0 && c->g.oy > 0;
+        for (size_t a = 0; a < vec.size(); ++a) {
+            F.nb[a] = (vec[a][2] * F.pyp + vec[a][1]) * F.pxp + vec[a][0];
+            for (int k = 0; k < 3; ++k) F.we[a][k] = (float)(w[a] * (double)vec[a][k]);
+        }
+        for (int i = 0; i < c->Q; ++i) {
+            int cv[3];
+            for (int k = 0; k < 3; ++k) cv[k] = c->Q == 9 ? vel9(i, k) : vel19(i, k);
+            F.pop[i] = (cv[2] * c->g.nyp + cv[1]) * c->g.nxp + cv[0];
+        }
     }
     c->n_groups = (int)gb.size();
     c->e2 = tmp.e2;

@@ -36,21 +36,27 @@ cudaError_t f32_step(lb_ctx *c) {
     float *B = (float *)c->f[1 - c->cur];
     float *psi = (float *)c->psi;
     int gb = grid_for(c->g.N);
-    if (c->Q == 9) {
+    if (!c->psi_halo) {   // beyond 32-bit node indices: the wrapped kernels
+        if (c->Q == 9) {
+            k_psi<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
+            k_collide<float, PairsF32, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pairs32, k, c->flags);
+        } else {
+            k_psi<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
+            k_collide<float, PairsF32, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pairs32, k, c->flags);
+        }
+    } else if (c->Q == 9) {
         tm_begin(c, LB_KERNEL_PSI);
-        k_psi<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
+        k_psi_f32<2, 9><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->pfast, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
-        k_collide<float, PairsF32, 2, 9, true>
-            <<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pairs32, k, c->flags);
+        k_collide_f32<2, 9><<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pfast, k, c->flags);
         tm_end(c);
     } else {
         tm_begin(c, LB_KERNEL_PSI);
-        k_psi<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
+        k_psi_f32<3, 19><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->pfast, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
-        k_collide<float, PairsF32, 3, 19, true>
-            <<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pairs32, k, c->flags);
+        k_collide_f32<3, 19><<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pfast, k, c->flags);
         tm_end(c);
     }
     c->launches += 2;

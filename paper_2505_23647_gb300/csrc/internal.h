@@ -27,6 +27,22 @@ struct PairsF32 {
     signed char v[MAXP][3];
     float w[MAXP];
 };
+// The binary32 stencil of the generic kernels, ready for nodes at least R
+// from every boundary: per pair the site offset of e_a and W_a e_a folded
+// per component (the force is three FMAs per pair), and the population
+// index offsets of the pulls A_i(x - xi_i).  Boundary nodes use PairsF32.
+struct PairsFast {
+    int npairs, R;
+    int nb[MAXP];         // offsets of e_a in the halo'd psi field
+    float we[MAXP][3];
+    int pop[19];
+    int H, Hz;            // psi halo in x, y and in z (0 in 2D)
+    int pxp, pyp;         // halo'd psi row and plane extents
+    int pull_pad;         // populations carry x/y ghosts: only z needs wrapping
+};
+// binary32 psi fields of the generic kernels carry a periodic halo of
+// PSI_HALO nodes on every side (x, y and, in 3D, z)
+constexpr int PSI_HALO = LB_MAX_RADIUS;
 
 // Per-context constants of the collision (formed on the host once, in the
 // same expressions as the reference: omega = 1/tau, cw_i = (1 - 1/(2 tau)) w_i).
@@ -130,6 +146,7 @@ struct lb_ctx {
     sclbm::Consts k;
     sclbm::PairsF64 pairs64;
     sclbm::PairsF32 pairs32;
+    sclbm::PairsFast pfast;
     int n_groups;
     double e2;                // second moment of the stencil (lb_stencil_info.e2)
     int group_base[LB_MAX_PAIRS][3];
@@ -149,7 +166,9 @@ struct lb_ctx {
     CUtensorMap tmap[2][2];   // [buffer][R-1] plane boxes of TY + 2R rows
     void *f[2];               // population buffers [Q][N] (post-collision, pre-stream)
     int cur;                  // buffer holding the current state
-    void *psi;                // [N] psi of the precision in use
+    void *psi;                // psi of the precision in use: [N], or for binary32 with
+                              // a halo of psi_halo nodes per side (PairsFast)
+    int psi_halo;
     double *red;              // reduction partials and small results (128 KB)
     sclbm::Flags *flags;      // device counters
     cudaStream_t stream;

@@ -262,6 +262,120 @@ __global__ void __launch_bounds__(256) k_collide(const T *__restrict__ A, T *__r
     if (blockIdx.x == 0 && threadIdx.x == 0) flags->step = flags->step + 1;
 }
 
+// ---------------------------------------------------------------------------
+// Generic binary32 kernels (any stencil up to radius 4): psi is kept with a
+// periodic halo, so every node takes the force as three FMAs per pair from
+// fixed offsets and the folded weights W_a e_a; pulls use fixed offsets
+// except where a periodic wrap is needed.  Coordinates in 32-bit arithmetic
+// (the launcher requires fewer than 2^31 halo'd psi nodes).
+__device__ __forceinline__ void coords32(const Geom &g, int s, int &x, int &y, int &z) {
+    const int q = s / g.nx;
+    x = s - q * g.nx;
+    z = q / g.ny;
+    y = q - z * g.ny;
+}
+
+// index of node (x, y, z) in the halo'd binary32 psi field
+__device__ __forceinline__ int psi_at(const PairsFast &P, int x, int y, int z) {
+    return ((z + P.Hz) * P.pyp + (y + P.H)) * P.pxp + (x + P.H);
+}
+
+// Force sums of eq. sc_f at psi index sp (any node: the halo holds the
+// periodic images), three FMAs per pair with the folded weights W_a e_a.
+template <int D>
+__device__ __forceinline__ void force_fast(const float *__restrict__ psi, int sp, const PairsFast &P,
+                                           float *acc) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 4
+    for (int a = 0; a < P.npairs; ++a) {
+        const float d = psi[sp + P.nb[a]] - psi[sp - P.nb[a]];
+        a0 = fmaf(P.we[a][0], d, a0);
+        a1 = fmaf(P.we[a][1], d, a1);
+        if (D == 3) a2 = fmaf(P.we[a][2], d, a2);
+    }
+    acc[0] = a0;
+    acc[1] = a1;
+    acc[2] = a2;
+}
+
+// pulls A_i(x - xi_i): fixed offsets unless a periodic wrap is needed (x or
+// y on an unpadded boundary, z on a boundary plane)
+template <int D, int Q>
+__device__ __forceinline__ void pull_f32(const float *__restrict__ A, const Geom &g, int x, int y,
+                                         int z, const PairsFast &P, float *fi) {
+    const bool zin = D == 2 || (z >= 1 && z < g.nz - 1);
+    const bool in = zin && (P.pull_pad || (x >= 1 && x < g.nx - 1 && y >= 1 && y < g.ny - 1));
+    if (in) {
+        const long long ps = ((long long)z * g.nyp + (y + g.oy)) * g.nxp + (x + g.ox);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) fi[i] = A[(long long)i * g.Np + ps - P.pop[i]];
+    } else {
+        pull<float, D, Q>(A, g, x, y, z, fi);
+    }
+}
+
+// psi of every node into the halo'd field, with its periodic images
+template <int D, int Q>
+__global__ void __launch_bounds__(256) k_psi_f32(const float *__restrict__ A, float *__restrict__ psi,
+                                                 Geom g, float rho0, const PairsFast P,
+                                                 Flags *flags, PsiK pk) {
+    const int N = (int)g.N, stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += stride) {
+        int x, y, z;
+        coords32(g, s, x, y, z);
+        float fi[Q];
+        pull_f32<D, Q>(A, g, x, y, z, P, fi);
+        const float n = sum_q<float, Q>(fi) + rho0;
+        if (!(n > 0.f)) atomicMin(&flags->err_step, flags->step);
+        const float v = psi_eval<float>(n, pk, &flags->exp_amb);
+        // the images x + kx nx (y, z likewise) that fall inside the halo
+        const int kx = (P.H + g.nx - 1) / g.nx, ky = (P.H + g.ny - 1) / g.ny;
+        const int kz = D == 3 ? (P.Hz + g.nz - 1) / g.nz : 0;
+        for (int c = -kz; c <= kz; ++c) {
+            const int zz = z + c * g.nz;
+            if (zz < -P.Hz || zz >= g.nz + P.Hz) continue;
+            for (int b = -ky; b <= ky; ++b) {
+                const int yy = y + b * g.ny;
+                if (yy < -P.H || yy >= g.ny + P.H) continue;
+                for (int a = -kx; a <= kx; ++a) {
+                    const int xx = x + a * g.nx;
+                    if (xx < -P.H || xx >= g.nx + P.H) continue;
+                    psi[psi_at(P, xx, yy, zz)] = v;
+                }
+            }
+        }
+    }
+}
+
+template <int D, int Q>
+__global__ void __launch_bounds__(256) k_collide_f32(const float *__restrict__ A, float *__restrict__ B,
+                                                     const float *__restrict__ psi, Geom g,
+                                                     const PairsFast PF, const ConstsT<float> k,
+                                                     Flags *flags) {
+    const int N = (int)g.N, stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += stride) {
+        int x, y, z;
+        coords32(g, s, x, y, z);
+        float fi[Q];
+        pull_f32<D, Q>(A, g, x, y, z, PF, fi);
+        const float dn = sum_q<float, Q>(fi);
+        const float n = dn + k.rho0;
+        const int sp = psi_at(PF, x, y, z);
+        float acc[3];
+        force_fast<D>(psi, sp, PF, acc);
+        const float pre = k.mGp * psi[sp];
+        float F[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
+        float fo[Q];
+        collide<float, D, Q, true>(fi, n, dn, F, k, fo, nullptr, nullptr);
+        const long long ps = ((long long)z * g.nyp + (y + g.oy)) * g.nxp + (x + g.ox);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) B[(long long)i * g.Np + ps] = fo[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags->step = flags->step + 1;
+}
+
 // Density and psi in binary64 from a state of either precision.
 template <typename T, int D, int Q, bool SHIFT>
 __global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,

@@ -28,6 +28,9 @@
 // and the reduction partials and results in the context's reduction buffer.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdlib>
+
 #include "kernels.cuh"
 
 namespace sclbm {
@@ -104,45 +107,104 @@ __device__ __forceinline__ double sum_q_exactish(const float *fi) {
     return (double)s + (double)err;
 }
 
+// Index offsets of a node's neighbours that need no periodic wrap: pulled
+// populations A_i(x - xi_i) relative to the node's own population index, and
+// the stencil's psi neighbours psi(x + e_a) relative to its site index.
+struct ObsOff {
+    int pop[19];
+    int nb[MAXP];
+    int R;          // nodes at least R from every boundary use the offsets
+};
+
 // One pass: per node n (binary64), F from the psi field, u and j + F/2 in the
-// context's precision T; accumulated as Red.  Grid-stride order over nodes,
-// NB_OBS blocks of 256 threads.
+// context's precision T; accumulated per thread (binary64; compensated for
+// binary64 lattices), then per block by warp shuffles.  Block b takes the
+// rows (y, z) b, b + NB_OBS, ..., thread t the columns t, t + 256, ...: a
+// fixed order, so the result does not depend on timing.
 constexpr int NB_OBS = 1024;
 
 template <typename T, typename PairsT, int D, int Q, bool SHIFT>
 __global__ void __launch_bounds__(256) k_obs(const T *__restrict__ A, Geom g,
                                              const T *__restrict__ psi, const PairsT P,
+                                             const ObsOff off, const PairsFast PF,
                                              const ConstsT<T> k, Red *partial) {
     Red r = red_zero();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
-        int x, y, z;
-        coords(g, s, x, y, z);
-        T fi[Q];
-        pull<T, D, Q>(A, g, x, y, z, fi);
-        const T dn = sum_q<T, Q>(fi);
-        const T n = SHIFT ? dn + k.rho0 : dn;
-        double n64;
-        if constexpr (SHIFT) n64 = sum_q_exactish<Q>(fi) + (double)k.rho0;
-        else n64 = (double)n;
-        T acc[3];
-        force_acc<T, PairsT, D>(psi, g, x, y, z, P, acc);
-        const T pre = k.mGp * psi[s];
-        T F[3] = {T(0), T(0), T(0)};
+    double mass = 0.0, mom[3] = {0.0, 0.0, 0.0};   // binary32 lattices: plain sums
+    const int rows = g.ny * g.nz;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = row % g.ny, z = row / g.ny;
+        const bool yz_in = y >= off.R && y < g.ny - off.R &&
+                           (D == 2 || (z >= off.R && z < g.nz - off.R));
+        const long long prow = ((long long)z * g.nyp + (y + g.oy)) * g.nxp + g.ox;
+        for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+            const bool in = yz_in && x >= off.R && x < g.nx - off.R;
+            const long long s = (long long)row * g.nx + x;
+            T fi[Q];
+            if constexpr (SHIFT) {
+                pull_f32<D, Q>(A, g, x, y, z, PF, fi);
+            } else if (in) {
 #pragma unroll
-        for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
-        T u[3], m[3];
-        collide<T, D, Q, SHIFT>(fi, n, dn, F, k, nullptr, u, m);
-        r.mass = dd_add(r.mass, dd_two_sum(n64, 0.0));
-        double uu = (double)u[0] * (double)u[0];
+                for (int i = 0; i < Q; ++i) fi[i] = A[(long long)i * g.Np + prow + x - off.pop[i]];
+            } else {
+                pull<T, D, Q>(A, g, x, y, z, fi);
+            }
+            const T dn = sum_q<T, Q>(fi);
+            const T n = SHIFT ? dn + k.rho0 : dn;
+            T acc[3] = {T(0), T(0), T(0)};
+            long long sp = s;   // own psi index (halo'd field for binary32)
+            if constexpr (SHIFT) {
+                sp = psi_at(PF, x, y, z);
+                force_fast<D>(psi, (int)sp, PF, acc);
+            } else if (in) {
+                for (int a = 0; a < P.npairs; ++a) {
+                    const T t = P.w[a] * (psi[s + off.nb[a]] - psi[s - off.nb[a]]);
 #pragma unroll
-        for (int mu = 0; mu < D; ++mu) {
-            if (mu) uu = uu + (double)u[mu] * (double)u[mu];
-            r.mom[mu] = dd_add(r.mom[mu], ddv{(double)m[mu], 0.0});
+                    for (int mu = 0; mu < D; ++mu) {
+                        const int c = P.v[a][mu];
+                        if (c == 1) acc[mu] = acc[mu] + t;
+                        else if (c == -1) acc[mu] = acc[mu] - t;
+                        else if (c == 2) acc[mu] = acc[mu] + (t + t);
+                        else if (c == -2) acc[mu] = acc[mu] - (t + t);
+                        else if (c != 0) acc[mu] = acc[mu] + t * T(c);
+                    }
+                }
+            } else {
+                force_acc<T, PairsT, D>(psi, g, x, y, z, P, acc);
+            }
+            const T pre = k.mGp * psi[sp];
+            T F[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
+            T u[3], m[3];
+            collide<T, D, Q, SHIFT>(fi, n, dn, F, k, nullptr, u, m);
+            double n64;
+            if constexpr (SHIFT) {
+                n64 = sum_q_exactish<Q>(fi) + (double)k.rho0;
+                mass = mass + n64;
+                float uu = u[0] * u[0];
+#pragma unroll
+                for (int mu = 1; mu < D; ++mu) uu = uu + u[mu] * u[mu];
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) mom[mu] = mom[mu] + (double)m[mu];
+                r.umax2 = fmax(r.umax2, (double)uu);
+            } else {
+                n64 = (double)n;
+                r.mass = dd_add(r.mass, dd_two_sum(n64, 0.0));
+                double uu = (double)u[0] * (double)u[0];
+#pragma unroll
+                for (int mu = 0; mu < D; ++mu) {
+                    if (mu) uu = uu + (double)u[mu] * (double)u[mu];
+                    r.mom[mu] = dd_add(r.mom[mu], ddv{(double)m[mu], 0.0});
+                }
+                r.umax2 = fmax(r.umax2, uu);
+            }
+            r.rmin = fmin(r.rmin, n64);
+            r.rmax = fmax(r.rmax, n64);
         }
-        r.umax2 = fmax(r.umax2, uu);
-        r.rmin = fmin(r.rmin, n64);
-        r.rmax = fmax(r.rmax, n64);
+    }
+    if constexpr (SHIFT) {
+        r.mass = ddv{mass, 0.0};
+        for (int mu = 0; mu < 3; ++mu) r.mom[mu] = ddv{mom[mu], 0.0};
     }
     r = red_block(r);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -167,33 +229,56 @@ double *obs_results(lb_ctx *c) {
     return reinterpret_cast<double *>(reinterpret_cast<char *>(c->red) + NB_OBS * sizeof(Red));
 }
 
+static ObsOff obs_offsets(const lb_ctx *c) {
+    ObsOff o;
+    const Geom &g = c->g;
+    for (int i = 0; i < 19; ++i) {
+        const int cx = i < c->Q ? (c->Q == 9 ? cvel<9>(i, 0) : cvel<19>(i, 0)) : 0;
+        const int cy = i < c->Q ? (c->Q == 9 ? cvel<9>(i, 1) : cvel<19>(i, 1)) : 0;
+        const int cz = i < c->Q ? (c->Q == 9 ? cvel<9>(i, 2) : cvel<19>(i, 2)) : 0;
+        o.pop[i] = (cz * g.nyp + cy) * g.nxp + cx;
+    }
+    int R = 1;
+    for (int a = 0; a < MAXP; ++a) {
+        if (a >= c->pairs64.npairs) { o.nb[a] = 0; continue; }
+        const int ex = c->pairs64.v[a][0], ey = c->pairs64.v[a][1], ez = c->pairs64.v[a][2];
+        o.nb[a] = (ez * g.ny + ey) * g.nx + ex;
+        const int m = std::max(std::abs(ex), std::max(std::abs(ey), std::abs(ez)));
+        R = std::max(R, m);
+    }
+    o.R = R;
+    return o;
+}
+
 cudaError_t obs_fused(lb_ctx *c) {
     static_assert(NB_OBS * sizeof(Red) + 64 * sizeof(double) <= 1024 * 128,
                   "reduction buffer too small");
     Red *part = reinterpret_cast<Red *>(c->red);
     double *res = obs_results(c);
     int gb = grid_for(c->g.N);
+    const ObsOff off = obs_offsets(c);
     if (c->p.precision == LB_FP64) {
         const double *A = (const double *)c->f[c->cur];
         double *psi = (double *)c->psi;
         auto k = consts_as<double>(c->k);
         if (c->Q == 9) {
             k_psi<double, 2, 9, false><<<gb, 256, 0, c->stream>>>(A, psi, c->g, 0.0, c->flags, psik(c));
-            k_obs<double, PairsF64, 2, 9, false><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs64, k, part);
+            k_obs<double, PairsF64, 2, 9, false><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs64, off, c->pfast, k, part);
         } else {
             k_psi<double, 3, 19, false><<<gb, 256, 0, c->stream>>>(A, psi, c->g, 0.0, c->flags, psik(c));
-            k_obs<double, PairsF64, 3, 19, false><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs64, k, part);
+            k_obs<double, PairsF64, 3, 19, false><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs64, off, c->pfast, k, part);
         }
     } else {
+        if (!c->psi_halo) return cudaErrorNotSupported;   // beyond 32-bit node indices
         const float *A = (const float *)c->f[c->cur];
         float *psi = (float *)c->psi;
         auto k = consts_as<float>(c->k);
         if (c->Q == 9) {
-            k_psi<float, 2, 9, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
-            k_obs<float, PairsF32, 2, 9, true><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs32, k, part);
+            k_psi_f32<2, 9><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->pfast, c->flags, psik(c));
+            k_obs<float, PairsF32, 2, 9, true><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs32, off, c->pfast, k, part);
         } else {
-            k_psi<float, 3, 19, true><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->flags, psik(c));
-            k_obs<float, PairsF32, 3, 19, true><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs32, k, part);
+            k_psi_f32<3, 19><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->pfast, c->flags, psik(c));
+            k_obs<float, PairsF32, 3, 19, true><<<NB_OBS, 256, 0, c->stream>>>(A, c->g, psi, c->pairs32, off, c->pfast, k, part);
         }
     }
     k_obs_final<<<1, 256, 0, c->stream>>>(NB_OBS, part, res);
