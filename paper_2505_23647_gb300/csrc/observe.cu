@@ -415,7 +415,7 @@ template <typename T, int D, int Q, bool SHIFT>
 __global__ void __launch_bounds__(128) k_profile_rows(const T *__restrict__ A, Geom g, double rho0,
                                                       const double *__restrict__ psi,
                                                       const PTPairs P, int rows, int rpb,
-                                                      double *__restrict__ part) {
+                                                      double *__restrict__ part, int direct) {
     constexpr int NC = D == 2 ? 3 : 6;
     constexpr int YY = D == 2 ? 2 : 3;
     const int r0 = blockIdx.x * rpb, r1 = min(r0 + rpb, rows);
@@ -430,8 +430,14 @@ __global__ void __launch_bounds__(128) k_profile_rows(const T *__restrict__ A, G
             sxx = dd_add(sxx, ddv{Ps[0], 0.0});
             syy = dd_add(syy, ddv{Ps[YY], 0.0});
         }
-        double *o = part + ((long long)blockIdx.x * g.nx + x) * 6;
-        o[0] = sn.hi; o[1] = sn.lo; o[2] = sxx.hi; o[3] = sxx.lo; o[4] = syy.hi; o[5] = syy.lo;
+        if (direct) {   // one block of rows: the means straight into the profiles
+            part[x] = (sn.hi + sn.lo) / rows;
+            part[g.nx + x] = (sxx.hi + sxx.lo) / rows;
+            part[2 * g.nx + x] = (syy.hi + syy.lo) / rows;
+        } else {
+            double *o = part + ((long long)blockIdx.x * g.nx + x) * 6;
+            o[0] = sn.hi; o[1] = sn.lo; o[2] = sxx.hi; o[3] = sxx.lo; o[4] = syy.hi; o[5] = syy.lo;
+        }
     }
 }
 
@@ -544,29 +550,33 @@ cudaError_t flat_interfaces(lb_ctx *c, int maxw, lb_flat_obs *out_dev, int *coun
     const long long N = c->g.N;
     const int nx = c->g.nx, rows = c->g.ny * c->g.nz;
     double *psi = stage_ptr(c);
-    // staging: psi [N], partials [nb][nx][6], profiles [3][nx]
+    // staging: psi [N], partials [nb][nx][6] (unless direct), profiles [3][nx]
     const size_t cap = stage_bytes(c) / sizeof(double);
     long long room = (long long)cap - N - 3LL * nx;
     long long nbl = room / (6LL * nx);
     if (nbl > rows) nbl = rows;
     if (nbl > 256) nbl = 256;
-    int nb = (int)nbl;
-    if (nb < 1) return cudaErrorInvalidValue;
+    // too little room for partial sums (thin slabs): one block of rows
+    // writes the profiles directly
+    const int direct = nbl < 2;
+    if (direct && room < 0) return cudaErrorInvalidValue;
+    int nb = direct ? 1 : (int)nbl;
     const int rpb = (rows + nb - 1) / nb;
     nb = (rows + rpb - 1) / rpb;
-    double *part = psi + N, *prof = part + (long long)nb * nx * 6;
+    double *part = psi + N, *prof = direct ? part : part + (long long)nb * nx * 6;
     psi64_field(c, psi);
     const double r0 = c->k.rho0;
     if (c->p.precision == LB_FP64) {
         const double *A = (const double *)c->f[c->cur];
-        if (c->Q == 9) k_profile_rows<double, 2, 9, false><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part);
-        else k_profile_rows<double, 3, 19, false><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part);
+        if (c->Q == 9) k_profile_rows<double, 2, 9, false><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part, direct);
+        else k_profile_rows<double, 3, 19, false><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part, direct);
     } else {
         const float *A = (const float *)c->f[c->cur];
-        if (c->Q == 9) k_profile_rows<float, 2, 9, true><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part);
-        else k_profile_rows<float, 3, 19, true><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part);
+        if (c->Q == 9) k_profile_rows<float, 2, 9, true><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part, direct);
+        else k_profile_rows<float, 3, 19, true><<<nb, 128, 0, c->stream>>>(A, c->g, r0, psi, P, rows, rpb, part, direct);
     }
-    k_profile_sum<<<(nx + 127) / 128, 128, 0, c->stream>>>(part, nb, nx, (double)rows, prof);
+    if (!direct)
+        k_profile_sum<<<(nx + 127) / 128, 128, 0, c->stream>>>(part, nb, nx, (double)rows, prof);
     k_flat_windows<<<1, 1, 0, c->stream>>>(prof, nx, maxw, out_dev, count_dev);
     c->launches += 3;
     return cudaGetLastError();
