@@ -449,6 +449,31 @@ lb_status lb_adjoint_seed_sigma(lb_adjoint *adj, int n_interfaces, double *sigma
  * z_e - z_s of a flat interface.  LB_EUNSUPPORTED for stencil groups
  * outside Appendices E/F. */
 lb_status lb_adjoint_seed_pt(lb_adjoint *adj, const double *m, double *value);
+/* Quantities of a flat slab (gradients along x) for lb_adjoint_seed_flat. */
+enum {
+    LB_FLAT_SIGMA = 0,  /* sigma_0: sum over the line of P_N - P_T / #interfaces (eq. sigma0pnpt) */
+    LB_FLAT_DELTA = 1,  /* Tolman length z_e - z_s, mean over the interfaces (eqs. zemzs, SCTolmanFlat) */
+    LB_FLAT_WIDTH = 2,  /* 6 sum_x (n - n_g)(n_l - n) / (n_l - n_g)^2 / #interfaces (n: y(z)-mean
+                           profile; equals w for a tanh profile of width w); params: n_l, n_g,
+                           #interfaces (<= 0: the number found) */
+    LB_FLAT_RATIO = 3   /* n(x_l) / n(x_g) of the profile; params: x_l, x_g (columns) */
+};
+
+/* Add weight * dQ/d(state) to lam, and weight * Q's explicit dependence on W
+ * and G to the gradients, for one quantity Q of the current state of a flat
+ * slab: the profiles of n and P_N - P_T (y(z) means, binary64 lattice
+ * pressure tensor, Appendices E/F), the interface windows and Q and its
+ * per-column derivatives are formed on the device (the windows and
+ * integrals of lb_flat_interfaces).  The density part seeds lam through
+ * n = sum_i f_i, the tensor part through the adjoint of the per-site
+ * tensor (as lb_adjoint_seed_pt).  Seeds add up, so several quantities
+ * with weights g_k give the gradient of sum_k g_k Q_k in one lb_adjoint_run
+ * sweep.  *value (may be NULL) receives Q (not weighted).  params: host
+ * doubles as listed above (may be NULL for SIGMA, DELTA).  LB_EINVAL for a
+ * bad quantity or parameters or a state without an interface;
+ * LB_EUNSUPPORTED for stencil groups outside Appendices E/F. */
+lb_status lb_adjoint_seed_flat(lb_adjoint *adj, int quantity, const double *params, double weight,
+                               double *value);
 /* Carry lam back over the next nsteps steps of the context (see above). */
 lb_status lb_adjoint_run(lb_adjoint *adj, int nsteps);
 /* dL/dW per stencil group (n_groups doubles, may be NULL) and dL/dG. */

@@ -118,6 +118,7 @@ _SIGS = {
     "lb_adjoint_zero_grad": ([_vp], ctypes.c_int),
     "lb_adjoint_seed_sigma": ([_vp, ctypes.c_int, _dp], ctypes.c_int),
     "lb_adjoint_seed_pt": ([_vp, _dp, _dp], ctypes.c_int),
+    "lb_adjoint_seed_flat": ([_vp, ctypes.c_int, _dp, ctypes.c_double, _dp], ctypes.c_int),
     "lb_adjoint_run": ([_vp, ctypes.c_int], ctypes.c_int),
     "lb_adjoint_gradient": ([_vp, _dp, _dp], ctypes.c_int),
     "lb_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp, ctypes.POINTER(_vp)],

@@ -1,15 +1,20 @@
-"""Gradients of the flat-interface surface tension through the step
-(``lb_adjoint_*``), with checkpointed recomputation, and a
-``torch.autograd.Function`` on top.
+"""Gradients of flat-interface quantities through the step (``lb_adjoint_*``),
+with checkpointed recomputation, and a ``torch.autograd.Function`` on top.
 
-Every step, forward and backward, runs in the library's kernels; this module
-only moves checkpoints (``lb_get_state`` / ``lb_set_state``) and arguments.
+Every step, forward and backward, runs in the library's kernels, and so does
+the post-processing of the quantities (profiles, interface windows, sigma_0,
+the Tolman length, the interface width, the density ratio and their seeds:
+``lb_adjoint_seed_flat``, binary64 on the device); this module only moves
+checkpoints (``lb_get_state`` / ``lb_set_state``) and arguments.
 """
 import ctypes
 
 import numpy as np
 
 from . import LbError, Lattice, _check, _lib, _ptr, _vp
+
+# quantities of lb_adjoint_seed_flat
+LB_FLAT_SIGMA, LB_FLAT_DELTA, LB_FLAT_WIDTH, LB_FLAT_RATIO = range(4)
 
 
 class Adjoint:
@@ -51,6 +56,19 @@ class Adjoint:
             raise ValueError("m must have N entries")
         v = ctypes.c_double(0.0)
         _check(_lib.lb_adjoint_seed_pt(_vp(self.a), _ptr(m), ctypes.byref(v)), "lb_adjoint_seed_pt")
+        return v.value
+
+    def seed_flat(self, quantity, params=None, weight=1.0):
+        """Add weight x the gradient of a flat-slab quantity (LB_FLAT_*) of the
+        current state to lam; returns the quantity (computed on the device)."""
+        v = ctypes.c_double(0.0)
+        if params is None:
+            pp = None
+        else:
+            arr = np.ascontiguousarray(np.asarray(params, dtype=np.float64).ravel())
+            pp = _ptr(arr)
+        _check(_lib.lb_adjoint_seed_flat(_vp(self.a), int(quantity), pp, float(weight),
+                                         ctypes.byref(v)), "lb_adjoint_seed_flat")
         return v.value
 
     def run(self, nsteps):
@@ -133,63 +151,9 @@ def density_functional_and_gradient(lattice, steps, fn, checkpoint_every=100):
     return value, dW, dG, lam0
 
 
-def density_ratio(x_liquid, x_gas):
-    """L(n) = n_l / n_g of a flat slab (gradients along x): the densities are
-    the y (and z) averages of columns x_liquid and x_gas."""
-    def fn(n):
-        cols = n.shape[0] * n.shape[1]
-        nl, ng = n[..., x_liquid].mean(), n[..., x_gas].mean()
-        d = np.zeros_like(n)
-        d[..., x_liquid] = 1.0 / (ng * cols)
-        d[..., x_gas] = -nl / (ng * ng * cols)
-        return nl / ng, d
-    return fn
-
-
-def interface_width(n_liquid, n_gas, n_interfaces=2):
-    """Smooth width of the interfaces of a flat slab (gradients along x):
-    L(n) = 6 sum_x (n(x) - n_g)(n_l - n(x)) / (n_l - n_g)^2 / #interfaces with
-    n(x) the y (and z) average; for a tanh profile of width w it equals w."""
-    def fn(n):
-        cols = n.shape[0] * n.shape[1]
-        prof = n.mean(axis=(0, 1))
-        dl = n_liquid - n_gas
-        val = 6.0 * float(np.sum((prof - n_gas) * (n_liquid - prof))) / (dl * dl) / n_interfaces
-        dprof = 6.0 * (n_liquid + n_gas - 2.0 * prof) / (dl * dl) / n_interfaces
-        return val, np.broadcast_to(dprof / cols, n.shape).copy()
-    return fn
-
-
-def _windows(prof):
-    """Interface windows of a periodic profile: for each crossing of the mid
-    density between x and x+1, the columns from half way to the previous
-    crossing to half way to the next one; +1 for gas -> liquid along +x."""
-    L = len(prof)
-    mid = 0.5 * (prof.max() + prof.min())
-    sg = np.sign(prof - mid)
-    cross = [(i, 1 if sg[(i + 1) % L] > sg[i] else -1) for i in range(L)
-             if sg[i] != sg[(i + 1) % L] and sg[i] != 0 and sg[(i + 1) % L] != 0]
-    out = []
-    k = len(cross)
-    for q, (i, d) in enumerate(cross):
-        gp = (i - cross[q - 1][0]) % L if k > 1 else L
-        gn = (cross[(q + 1) % k][0] - i) % L if k > 1 else L
-        out.append((i - gp // 2 + 1, i + gn // 2, d))
-    return out
-
-
-def tolman_and_gradient(lattice, steps, checkpoint_every=100):
-    """Tolman length delta = z_e - z_s of a flat slab (gradients along x) after
-    ``steps`` steps, averaged over its interfaces, and its gradient with
-    respect to the stencil group weights, G and the initial state.
-
-    Per interface window (columns a..b, site x the cell [x - 1/2, x + 1/2]):
-    z_s = sum x (P_N - P_T) / sum (P_N - P_T) from the lattice pressure tensor
-    (Appendices E/F), z_e the equimolar position from the window-end
-    densities, delta oriented from liquid to gas (eqs. zemzs, SCTolmanFlat).
-    The loss is a function of the column-averaged density and of
-    P_N - P_T: its density part seeds lam, its tensor part enters through
-    lb_adjoint_seed_pt.  Returns (delta, dW, dG, d delta/d(initial state))."""
+def forward_with_checkpoints(lattice, steps, checkpoint_every=100):
+    """Step ``lattice`` ``steps`` steps, keeping its state every
+    ``checkpoint_every`` steps: [(step, state), ...]."""
     K = max(1, int(checkpoint_every))
     ckpts = []
     done = 0
@@ -198,87 +162,86 @@ def tolman_and_gradient(lattice, steps, checkpoint_every=100):
         k = min(K, steps - done)
         lattice.step(k)
         done += k
-    n, _ = lattice.fields()
-    P = lattice.pressure_tensor()
-    D = P[0] - (P[2] if lattice.D == 2 else P[3])
-    cols = n.shape[0] * n.shape[1]
-    prof, dprof = n.mean(axis=(0, 1)), D.mean(axis=(0, 1))
-    L = len(prof)
-    wins = _windows(prof)
-    if not wins:
-        raise ValueError("no interface in the final state")
-    g_n = np.zeros(L)     # d delta / d profile
-    g_d = np.zeros(L)     # d delta / d (P_N - P_T) profile
-    delta = 0.0
-    for a, b, d in wins:
-        xs = np.arange(a, b + 1)
-        idx = xs % L
-        J = len(idx)
-        S = float(np.sum(dprof[idx]))
-        zs = float(np.sum(xs * dprof[idx])) / S
-        nv = prof[idx]
-        if d > 0:      # gas at a, liquid at b
-            T = float(np.sum(nv)) - J * nv[0]
-            Dl = nv[-1] - nv[0]
-            ze = (b + 0.5) - T / Dl
-            dT = np.ones(J)
-            dT[0] -= J
-            dD = np.zeros(J)
-            dD[-1], dD[0] = 1.0, -1.0
-            dze = -(dT * Dl - T * dD) / (Dl * Dl)
-        else:          # liquid at a, gas at b
-            T = float(np.sum(nv)) - J * nv[-1]
-            Dl = nv[0] - nv[-1]
-            ze = (a - 0.5) + T / Dl
-            dT = np.ones(J)
-            dT[-1] -= J
-            dD = np.zeros(J)
-            dD[0], dD[-1] = 1.0, -1.0
-            dze = (dT * Dl - T * dD) / (Dl * Dl)
-        orient = -d
-        delta += orient * (ze - zs)
-        np.add.at(g_n, idx, orient * dze)
-        np.add.at(g_d, idx, -orient * (xs - zs) / S)
-    nw = len(wins)
-    delta /= nw
-    g_n /= nw * cols
-    g_d /= nw * cols
+    return ckpts
+
+
+def backward_through(lattice, adj, ckpts, steps, checkpoint_every=100):
+    """Carry the adjoint back to the initial state, one checkpointed segment
+    at a time (each recomputed from its checkpoint by the library's step);
+    returns (dW, dG, dL/d(initial state))."""
+    K = max(1, int(checkpoint_every))
+    for start, st in reversed(ckpts):
+        lattice.set_state(st)
+        adj.run(min(K, steps - start))
+    dW, dG = adj.gradient()
+    return dW, dG, adj.get()
+
+
+def flat_quantity_and_gradient(lattice, steps, quantity, params=None, checkpoint_every=100):
+    """A flat-slab quantity (LB_FLAT_SIGMA, _DELTA, _WIDTH with params
+    (n_l, n_g, #interfaces), _RATIO with params (x_liquid, x_gas)) after
+    ``steps`` steps of ``lattice`` and its gradient with respect to the
+    stencil group weights, G and the initial state; the quantity and its
+    seed are formed by the library (lb_adjoint_seed_flat).  Returns
+    (value, dW [groups], dG, dvalue/d(initial state))."""
+    ckpts = forward_with_checkpoints(lattice, steps, checkpoint_every)
     adj = Adjoint(lattice)
     try:
-        adj.set(np.broadcast_to(g_n, (lattice.Q,) + lattice.shape))
-        adj.seed_pt(np.broadcast_to(g_d, lattice.shape))
-        for start, st in reversed(ckpts):
-            lattice.set_state(st)
-            adj.run(min(K, steps - start))
-        dW, dG = adj.gradient()
-        lam0 = adj.get()
+        value = adj.seed_flat(quantity, params)
+        dW, dG, lam0 = backward_through(lattice, adj, ckpts, steps, checkpoint_every)
     finally:
         adj.close()
-    return delta, dW, dG, lam0
+    return value, dW, dG, lam0
+
+
+def density_ratio(x_liquid, x_gas):
+    """Quantity spec of n_l / n_g of a flat slab (gradients along x): the y
+    (and z) averages of columns x_liquid and x_gas."""
+    return LB_FLAT_RATIO, (x_liquid, x_gas)
+
+
+def interface_width(n_liquid, n_gas, n_interfaces=2):
+    """Quantity spec of the smooth interface width of a flat slab:
+    6 sum_x (n(x) - n_g)(n_l - n(x)) / (n_l - n_g)^2 / #interfaces with n(x)
+    the y (and z) average; for a tanh profile of width w it equals w."""
+    return LB_FLAT_WIDTH, (n_liquid, n_gas, n_interfaces)
+
+
+def tolman_and_gradient(lattice, steps, checkpoint_every=100):
+    """Tolman length delta = z_e - z_s of a flat slab (gradients along x)
+    after ``steps`` steps, averaged over its interfaces, and its gradient
+    with respect to the stencil group weights, G and the initial state
+    (eqs. zemzs, SCTolmanFlat; z_s from the lattice pressure tensor of
+    Appendices E/F, z_e from the window-end densities).  Returns
+    (delta, dW, dG, d delta/d(initial state))."""
+    return flat_quantity_and_gradient(lattice, steps, LB_FLAT_DELTA, None, checkpoint_every)
 
 
 def slab_observables(make_lattice, steps, x_liquid, x_gas, n_liquid, n_gas, checkpoint_every=100):
     """The four quantities the stencil tuning of Sec. V targets, for a flat
     slab (gradients along x), with their gradients: values (sigma_0, delta,
     interface width, density ratio n_l/n_g), dW [4, groups] and dG [4].
-    ``make_lattice()`` returns a fresh lattice in the initial state (each
-    quantity runs its own forward and adjoint pass)."""
+    ``make_lattice()`` returns a fresh lattice in the initial state; one
+    forward run with checkpoints serves the four adjoint sweeps."""
+    specs = [(LB_FLAT_SIGMA, None), (LB_FLAT_DELTA, None),
+             interface_width(n_liquid, n_gas), density_ratio(x_liquid, x_gas)]
+    lat = make_lattice()
     vals, dWs, dGs = [], [], []
-    runs = [lambda lat: sigma_and_gradient(lat, steps, checkpoint_every),
-            lambda lat: tolman_and_gradient(lat, steps, checkpoint_every),
-            lambda lat: density_functional_and_gradient(lat, steps, interface_width(n_liquid, n_gas),
-                                                        checkpoint_every),
-            lambda lat: density_functional_and_gradient(lat, steps, density_ratio(x_liquid, x_gas),
-                                                        checkpoint_every)]
-    for run in runs:
-        lat = make_lattice()
-        try:
-            v, dW, dG, _ = run(lat)
-        finally:
-            lat.close()
-        vals.append(v)
-        dWs.append(dW)
-        dGs.append(dG)
+    try:
+        ckpts = forward_with_checkpoints(lat, steps, checkpoint_every)
+        final = lat.state()
+        for q, params in specs:
+            lat.set_state(final)
+            adj = Adjoint(lat)
+            try:
+                vals.append(adj.seed_flat(q, params))
+                dW, dG, _ = backward_through(lat, adj, ckpts, steps, checkpoint_every)
+            finally:
+                adj.close()
+            dWs.append(dW)
+            dGs.append(dG)
+    finally:
+        lat.close()
     return np.array(vals), np.array(dWs), np.array(dGs)
 
 
@@ -324,42 +287,89 @@ def _torch_function():
         return _FN
     import torch
 
-    class FlatSigma(torch.autograd.Function):
-        """sigma_0(W, G) of a flat slab after a fixed number of steps from a
-        fixed initial density; backward by the adjoint (computed with the
-        forward, checkpointed)."""
+    class FlatSlab(torch.autograd.Function):
+        """(sigma_0, delta, interface width, n_l/n_g) of a flat slab after a
+        fixed number of steps from a fixed initial density, as a function of
+        the stencil group weights W and G.  forward runs the steps (keeping
+        checkpoints) and measures the four quantities on the device;
+        backward seeds the adjoint with sum_k g_k dQ_k (one sweep back
+        through the checkpoints, whatever the number of outputs used)."""
 
         @staticmethod
         def forward(ctx, W, G, spec):
-            lat = Lattice(spec["lattice"], spec["shape"], spec["rho"], spec["bases"],
-                          W.detach().cpu().numpy().astype(np.float64), precision=spec.get("precision", "fp64"),
-                          tau=spec.get("tau", 1.0), G=float(G), convention=spec.get("convention", "literal"),
-                          psi_eps=spec.get("psi_eps"))
+            lat = _spec_lattice(spec, W.detach().cpu().numpy().astype(np.float64), float(G))
             try:
-                sigma, dW, dG, _ = sigma_and_gradient(lat, spec["steps"], spec.get("checkpoint_every", 100),
-                                                      spec.get("n_interfaces", 2))
+                ckpts = forward_with_checkpoints(lat, spec["steps"], spec.get("checkpoint_every", 100))
+                final = lat.state()
+                qs = _spec_quantities(spec)
+                adj = Adjoint(lat)
+                try:
+                    vals = [adj.seed_flat(q, p, 0.0) for q, p in qs]   # values only
+                finally:
+                    adj.close()
             finally:
                 lat.close()
-            ctx.save_for_backward(torch.as_tensor(dW, dtype=W.dtype), torch.as_tensor(dG, dtype=W.dtype))
-            return W.new_tensor(sigma)
+            ctx.spec = spec
+            ctx.ckpts = ckpts
+            ctx.final = final
+            ctx.save_for_backward(W, G)
+            return W.new_tensor(vals)
 
         @staticmethod
         def backward(ctx, g):
-            dW, dG = ctx.saved_tensors
-            return g * dW, g * dG, None
+            W, G = ctx.saved_tensors
+            spec = ctx.spec
+            lat = _spec_lattice(spec, W.detach().cpu().numpy().astype(np.float64), float(G))
+            try:
+                lat.set_state(ctx.final)
+                adj = Adjoint(lat)
+                try:
+                    for (q, p), gk in zip(_spec_quantities(spec), g.detach().cpu().numpy()):
+                        if gk != 0.0:
+                            adj.seed_flat(q, p, float(gk))
+                    dW, dG, _ = backward_through(lat, adj, ctx.ckpts, spec["steps"],
+                                                 spec.get("checkpoint_every", 100))
+                finally:
+                    adj.close()
+            finally:
+                lat.close()
+            return W.new_tensor(dW), G.new_tensor(dG), None
 
-    _FN = FlatSigma
-    return FlatSigma
+    _FN = FlatSlab
+    return FlatSlab
 
 
-def flat_sigma(W, G, spec):
-    """Differentiable sigma_0 (torch): W a tensor of group weights (the order
-    of spec['bases']), G a scalar tensor; spec holds lattice, shape, rho,
-    bases, steps and optionally precision, tau, convention, psi_eps,
-    checkpoint_every, n_interfaces."""
+def _spec_lattice(spec, W, G):
+    return Lattice(spec["lattice"], spec["shape"], spec["rho"], spec["bases"], W,
+                   precision=spec.get("precision", "fp64"), tau=spec.get("tau", 1.0), G=G,
+                   convention=spec.get("convention", "literal"), psi_eps=spec.get("psi_eps"))
+
+
+def _spec_quantities(spec):
+    nx = spec["shape"][0]
+    return [(LB_FLAT_SIGMA, None), (LB_FLAT_DELTA, None),
+            interface_width(spec.get("n_liquid", 0.0), spec.get("n_gas", 1.0),
+                            spec.get("n_interfaces", 2)),
+            density_ratio(spec.get("x_liquid", nx // 2), spec.get("x_gas", 0))]
+
+
+def flat_slab(W, G, spec):
+    """Differentiable (sigma_0, delta, interface width, n_l/n_g) of a flat slab
+    (torch, shape [4]): W a tensor of group weights (the order of
+    spec['bases']), G a scalar tensor; spec holds lattice, shape, rho, bases,
+    steps, n_liquid, n_gas (width reference), x_liquid, x_gas (ratio columns)
+    and optionally precision, tau, convention, psi_eps, checkpoint_every,
+    n_interfaces."""
     return _torch_function().apply(W, G, spec)
 
 
+def flat_sigma(W, G, spec):
+    """Differentiable sigma_0 alone (the first output of flat_slab)."""
+    return flat_slab(W, G, spec)[0]
+
+
 __all__ = ["Adjoint", "sigma_and_gradient", "density_functional_and_gradient", "density_ratio",
-           "interface_width", "tolman_and_gradient", "slab_observables", "tune_slab", "flat_sigma",
-           "LbError"]
+           "interface_width", "tolman_and_gradient", "flat_quantity_and_gradient",
+           "forward_with_checkpoints", "backward_through", "slab_observables", "tune_slab",
+           "flat_slab", "flat_sigma", "LB_FLAT_SIGMA", "LB_FLAT_DELTA", "LB_FLAT_WIDTH",
+           "LB_FLAT_RATIO", "LbError"]

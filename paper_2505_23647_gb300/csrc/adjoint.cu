@@ -279,6 +279,140 @@ __global__ void k_seed_pt(const double *__restrict__ psi, const double *__restri
     }
 }
 
+// Quantity Q of a slab and its per-column derivatives from the profiles
+// prof = [n][P^xx][P^yy] (means over y, z; one thread, nx columns):
+// gn[x] = dQ/d n(x), gd[x] = dQ/d (P_N - P_T)(x).  Interface windows as in
+// lb_flat_interfaces (crossings of the mid density, half way to the
+// neighbours); site x is the cell [x - 1/2, x + 1/2]; delta oriented from
+// liquid to gas.  val[0] = Q, val[1] = interfaces found.
+__global__ void k_flat_seed(const double *__restrict__ prof, int nx, int q, double p0, double p1,
+                            double p2, double *__restrict__ gn, double *__restrict__ gd,
+                            double *val) {
+    if (threadIdx.x || blockIdx.x) return;
+    const double *n = prof, *PN = prof + nx, *PT = prof + 2 * nx;
+    for (int x = 0; x < nx; ++x) gn[x] = gd[x] = 0.0;
+    double lo = n[0], hi = n[0];
+    for (int x = 1; x < nx; ++x) {
+        lo = fmin(lo, n[x]);
+        hi = fmax(hi, n[x]);
+    }
+    const double mid = 0.5 * (hi + lo);
+    auto sgn = [&](int x) { const double d = n[x] - mid; return d > 0.0 ? 1 : (d < 0.0 ? -1 : 0); };
+    auto cross = [&](int i) {
+        const int a = sgn(i), b = sgn((i + 1) % nx);
+        return a != b && a != 0 && b != 0;
+    };
+    int k = 0, last = -1, first = -1;
+    for (int i = 0; i < nx; ++i)
+        if (cross(i)) {
+            if (first < 0) first = i;
+            last = i;
+            ++k;
+        }
+    val[1] = k;
+    double Q = 0.0;
+    if (q == 0) {             // sigma_0: the whole line's P_N - P_T per interface
+        if (k == 0) { val[0] = nan(""); return; }
+        for (int x = 0; x < nx; ++x) {
+            Q = Q + (PN[x] - PT[x]);
+            gd[x] = 1.0 / k;
+        }
+        val[0] = Q / k;
+        return;
+    }
+    if (q == 1) {             // delta: per interface window
+        if (k == 0) { val[0] = nan(""); return; }
+        int prev = last;
+        for (int i = 0; i < nx; ++i) {
+            if (!cross(i)) continue;
+            int nxt = i;
+            for (int j = i + 1; j < i + 1 + nx; ++j)
+                if (cross(j % nx)) { nxt = j % nx; break; }
+            const int gp = k > 1 ? ((i - prev) % nx + nx) % nx : nx;
+            const int gq = k > 1 ? ((nxt - i) % nx + nx) % nx : nx;
+            const int wa = i - gp / 2 + 1, wb = i + gq / 2;
+            const bool rising = sgn((i + 1) % nx) > sgn(i);
+            prev = i;
+            auto at = [&](int x) { return ((x % nx) + nx) % nx; };
+            double S = 0.0, mom = 0.0;
+            for (int x = wa; x <= wb; ++x) {
+                const double d = PN[at(x)] - PT[at(x)];
+                S = S + d;
+                mom = mom + (double)x * d;
+            }
+            const double zs = mom / S;
+            const int J = wb - wa + 1;
+            double sumn = 0.0;
+            for (int x = wa; x <= wb; ++x) sumn = sumn + n[at(x)];
+            const double na = n[at(wa)], nb = n[at(wb)];
+            // z_e and its derivative in the window's densities
+            double ze, T, Dl;
+            if (rising) {   // gas at wa, liquid at wb
+                T = sumn - J * na;
+                Dl = nb - na;
+                ze = ((double)wb + 0.5) - T / Dl;
+            } else {        // liquid at wa, gas at wb
+                T = sumn - J * nb;
+                Dl = na - nb;
+                ze = ((double)wa - 0.5) + T / Dl;
+            }
+            const double orient = rising ? -1.0 : 1.0;
+            Q = Q + orient * (ze - zs);
+            for (int x = wa; x <= wb; ++x) {
+                const int xx = at(x);
+                // dT/dn(x) and dDl/dn(x)
+                double dT = 1.0, dD = 0.0;
+                if (rising) {
+                    if (x == wa) { dT -= J; dD -= 1.0; }
+                    if (x == wb) dD += 1.0;
+                } else {
+                    if (x == wb) { dT -= J; dD -= 1.0; }
+                    if (x == wa) dD += 1.0;
+                }
+                const double dze = (rising ? -1.0 : 1.0) * (dT * Dl - T * dD) / (Dl * Dl);
+                gn[xx] += orient * dze;
+                gd[xx] += -orient * ((double)x - zs) / S;
+            }
+        }
+        Q = Q / k;
+        for (int x = 0; x < nx; ++x) {
+            gn[x] /= k;
+            gd[x] /= k;
+        }
+    } else if (q == 2) {      // smooth interface width
+        const double nl = p0, ng = p1, ni = p2 > 0.0 ? p2 : (double)k;
+        if (!(ni > 0.0)) { val[0] = nan(""); return; }
+        const double dl = nl - ng;
+        for (int x = 0; x < nx; ++x) {
+            Q = Q + (n[x] - ng) * (nl - n[x]);
+            gn[x] = 6.0 * (nl + ng - 2.0 * n[x]) / (dl * dl) / ni;
+        }
+        Q = 6.0 * Q / (dl * dl) / ni;
+    } else {                  // density ratio n(x_l) / n(x_g)
+        const int xl = (int)p0, xg = (int)p1;
+        const double nl = n[xl], ng = n[xg];
+        Q = nl / ng;
+        gn[xl] += 1.0 / ng;
+        gn[xg] += -nl / (ng * ng);
+    }
+    val[0] = Q;
+}
+
+// lam_i(s) += w gn[x(s)] / rows (every i: n = sum_i f_i); m(s) = w gd[x(s)] / rows
+__global__ void k_broadcast_seed(double *__restrict__ lam, double *__restrict__ m,
+                                 const double *__restrict__ gn, const double *__restrict__ gd,
+                                 Geom g, int Q, double w) {
+    const double rows = (double)g.ny * g.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
+        const int x = (int)(s % g.nx);
+        const double a = w * gn[x] / rows;
+        if (a != 0.0)
+            for (int i = 0; i < Q; ++i) lam[(long long)i * g.N + s] += a;
+        m[s] = w * gd[x] / rows;
+    }
+}
+
 }  // namespace adj
 }  // namespace sclbm
 
@@ -465,11 +599,17 @@ lb_status lb_adjoint_seed_sigma(lb_adjoint *a, int n_interfaces, double *sigma) 
     return LB_OK;
 }
 
+namespace {
+// the tensor seed of lb_adjoint_seed_pt for site weights dm already on the
+// device (a->n, a->psi, a->dpsi hold the current state's fields)
+lb_status seed_pt_dev(lb_adjoint *a, const double *dm, double *value);
+}  // namespace
+
 lb_status lb_adjoint_seed_pt(lb_adjoint *a, const double *m, double *value) {
     if (!a || !m) return LB_EINVAL;
     lb_ctx *c = a->c;
-    static PTPairs P;   // host staging (large); calls are serialised per adjoint
-    if (!build_pt_pairs(c, &P)) return LB_EUNSUPPORTED;
+    PTPairs probe;
+    if (!build_pt_pairs(c, &probe)) return LB_EUNSUPPORTED;
     const long long N = a->g.N;
     double *dm = nullptr;
     cudaError_t e = cudaMalloc(&dm, N * sizeof(double));
@@ -481,10 +621,85 @@ lb_status lb_adjoint_seed_pt(lb_adjoint *a, const double *m, double *value) {
         return afail(e, "lb_adjoint_seed_pt");
     }
     lb_status s = fields_of(a, a->lam2);
-    if (s != LB_OK) {
-        cudaFree(dm);
-        return s;
+    if (s == LB_OK) s = seed_pt_dev(a, dm, value);
+    cudaFree(dm);
+    return s;
+}
+
+lb_status lb_adjoint_seed_flat(lb_adjoint *a, int quantity, const double *params, double weight,
+                               double *value) {
+    if (!a || quantity < LB_FLAT_SIGMA || quantity > LB_FLAT_RATIO || !std::isfinite(weight))
+        return LB_EINVAL;
+    if ((quantity == LB_FLAT_WIDTH || quantity == LB_FLAT_RATIO) && !params) return LB_EINVAL;
+    lb_ctx *c = a->c;
+    PTPairs probe;
+    if ((quantity == LB_FLAT_SIGMA || quantity == LB_FLAT_DELTA) && !build_pt_pairs(c, &probe))
+        return LB_EUNSUPPORTED;
+    const int nx = a->g.nx;
+    double p[3] = {0.0, 0.0, 0.0};
+    if (params) {
+        const int np = quantity == LB_FLAT_WIDTH ? 3 : (quantity == LB_FLAT_RATIO ? 2 : 0);
+        for (int k = 0; k < np; ++k) p[k] = params[k];
     }
+    if (quantity == LB_FLAT_RATIO &&
+        !(p[0] >= 0 && p[0] < nx && p[1] >= 0 && p[1] < nx && p[0] == (int)p[0] && p[1] == (int)p[1]))
+        return LB_EINVAL;
+    if (quantity == LB_FLAT_WIDTH && !(p[0] != p[1])) return LB_EINVAL;
+    // profiles of the current state (binary64, on the device)
+    double *buf = nullptr;   // prof [3 nx], gn [nx], gd [nx], val [2]
+    cudaError_t e = cudaMalloc(&buf, (5 * (size_t)nx + 2) * sizeof(double));
+    if (e != cudaSuccess) return afail(e, "lb_adjoint_seed_flat");
+    double *prof = buf, *gn = buf + 3 * nx, *gd = buf + 4 * nx, *val = buf + 5 * nx;
+    e = flat_profiles(c, prof, 0, nullptr, nullptr);
+    if (e == cudaErrorNotSupported) {
+        cudaFree(buf);
+        return LB_EUNSUPPORTED;
+    }
+    if (e == cudaSuccess) {
+        adj::k_flat_seed<<<1, 1, 0, c->stream>>>(prof, nx, quantity, p[0], p[1], p[2], gn, gd, val);
+        e = cudaGetLastError();
+    }
+    double hv[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hv, val, sizeof hv, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return afail(e, "lb_adjoint_seed_flat");
+    }
+    if (!std::isfinite(hv[0])) {
+        cudaFree(buf);
+        lb_set_error_message("lb_adjoint_seed_flat: no interface in the state");
+        return LB_EINVAL;
+    }
+    // the state's fields (for the tensor seed), then the seeds; lam2 is free
+    // once fields_of has read it and serves as the site weights m
+    e = c->p.precision == LB_FP64 ? f64_get_state(c, a->lam2, 0, c->Q) : f32_get_state(c, a->lam2, 0, c->Q);
+    lb_status s = e == cudaSuccess ? fields_of(a, a->lam2) : afail(e, "lb_adjoint_seed_flat");
+    if (s == LB_OK) {
+        adj::k_broadcast_seed<<<grid_for(a->g.N), 256, 0, c->stream>>>(a->lam, a->lam2, gn, gd, a->g,
+                                                                      a->Q, weight);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) s = afail(e, "lb_adjoint_seed_flat");
+    }
+    if (s == LB_OK && (quantity == LB_FLAT_SIGMA || quantity == LB_FLAT_DELTA)) {
+        double tv = 0.0;
+        s = seed_pt_dev(a, a->lam2, &tv);
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(buf);
+    if (s != LB_OK) return s;
+    if (value) *value = hv[0];
+    return LB_OK;
+}
+
+namespace {
+lb_status seed_pt_dev(lb_adjoint *a, const double *dm, double *value) {
+    lb_ctx *c = a->c;
+    static PTPairs P;   // host staging (large); calls are serialised per adjoint
+    if (!build_pt_pairs(c, &P)) return LB_EUNSUPPORTED;
+    const long long N = a->g.N;
+    lb_status s = LB_OK;
+    cudaError_t e;
     const int gb = grid_for(N);
     if (a->D == 2)
         adj::k_seed_pt<2, 9><<<gb, 256, 0, c->stream>>>(a->psi, a->dpsi, dm, a->g, P, a->pg, a->lam,
@@ -495,13 +710,13 @@ lb_status lb_adjoint_seed_pt(lb_adjoint *a, const double *m, double *value) {
     e = cudaGetLastError();
     double tot = 0.0;
     if (e == cudaSuccess) s = rowsums(a, a->snode, 1, &tot);
-    cudaFree(dm);
     if (e != cudaSuccess) return afail(e, "lb_adjoint_seed_pt");
     if (s != LB_OK) return s;
     a->dGp_direct += c->Gp != 0.0 ? tot / c->Gp : 0.0;
     if (value) *value = tot;
     return LB_OK;
 }
+}  // namespace
 
 lb_status lb_adjoint_run(lb_adjoint *a, int nsteps) {
     if (!a || nsteps < 0) return LB_EINVAL;

@@ -229,6 +229,9 @@ double *obs_results(lb_ctx *c);
 void psi64_field(lb_ctx *c, double *psi);  // binary64 psi of every node
 cudaError_t ptensor_field(lb_ctx *c, double *psi, double *out);
 cudaError_t flat_interfaces(lb_ctx *c, int maxw, lb_flat_obs *out_dev, int *count_dev);
+// profiles of n, P^xx, P^yy along x into prof_out (device [3][nx]); windows too if out_dev
+cudaError_t flat_profiles(lb_ctx *c, double *prof_out, int maxw, lb_flat_obs *out_dev,
+                          int *count_dev);
 cudaError_t curved_interface(lb_ctx *c, const double *center, double e2, lb_curved_obs *out_dev);
 // lattice pressure tensor of Appendices E/F, per pair (e, -e): A = psi(x) (psi(x+e) +
 // psi(x-e)), B = sum over the pair's links of psi(x+a) psi(x+b) (links prepared

@@ -545,6 +545,14 @@ __global__ void k_flat_windows(const double *__restrict__ prof, int nx, int maxw
 }
 
 cudaError_t flat_interfaces(lb_ctx *c, int maxw, lb_flat_obs *out_dev, int *count_dev) {
+    return flat_profiles(c, nullptr, maxw, out_dev, count_dev);
+}
+
+// The profiles of a slab along x -- means over y (and z) of n, P^xx, P^yy --
+// into prof_out (device, [3][nx]; NULL: kept in the staging buffer), and,
+// if out_dev, the interface windows and their integrals (k_flat_windows).
+cudaError_t flat_profiles(lb_ctx *c, double *prof_out, int maxw, lb_flat_obs *out_dev,
+                          int *count_dev) {
     static PTPairs P;
     if (!build_pt_pairs(c, &P)) return cudaErrorNotSupported;
     const long long N = c->g.N;
@@ -577,7 +585,12 @@ cudaError_t flat_interfaces(lb_ctx *c, int maxw, lb_flat_obs *out_dev, int *coun
     }
     if (!direct)
         k_profile_sum<<<(nx + 127) / 128, 128, 0, c->stream>>>(part, nb, nx, (double)rows, prof);
-    k_flat_windows<<<1, 1, 0, c->stream>>>(prof, nx, maxw, out_dev, count_dev);
+    if (prof_out) {
+        cudaError_t e = cudaMemcpyAsync(prof_out, prof, 3 * (size_t)nx * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (out_dev) k_flat_windows<<<1, 1, 0, c->stream>>>(prof, nx, maxw, out_dev, count_dev);
     c->launches += 3;
     return cudaGetLastError();
 }

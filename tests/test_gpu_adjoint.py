@@ -119,20 +119,42 @@ def test_fp32_forward_gradient_close_to_fp64():
 
 
 def test_torch_autograd_function():
+    """flat_slab: the four quantities in forward, one adjoint sweep for any
+    combination of them in backward; equal to the per-quantity gradients of
+    flat_quantity_and_gradient (and sigma_0 to the lattice-summed sigma of
+    lb_adjoint_seed_sigma divided by the rows)."""
     torch = pytest.importorskip("torch")
     lattice, shape, st, tau, G, conv, eps, steps = CASES[0]
+    nx, ny = shape
     spec = dict(lattice=lattice, shape=shape, rho=_rho(shape), bases=st.bases, steps=steps,
-                tau=tau, convention=conv, checkpoint_every=5)
+                tau=tau, convention=conv, checkpoint_every=5, n_liquid=N_LIQ, n_gas=N_GAS,
+                x_liquid=nx // 2, x_gas=1)
     W = torch.tensor(st.weights, dtype=torch.float64, requires_grad=True)
     Gt = torch.tensor(G, dtype=torch.float64, requires_grad=True)
-    s = AD.flat_sigma(W, Gt, spec)
-    (2.0 * s).backward()
+    q = AD.flat_slab(W, Gt, spec)
+    wts = np.array([2.0, 3.0, -1.0, 0.5])
+    (q * torch.tensor(wts)).sum().backward()
+    specs = [(AD.LB_FLAT_SIGMA, None), (AD.LB_FLAT_DELTA, None),
+             AD.interface_width(N_LIQ, N_GAS), AD.density_ratio(nx // 2, 1)]
+    dW_sum, dG_sum = 0.0, 0.0
+    for k, (qq, pp) in enumerate(specs):
+        lat = _lat(lattice, shape, st, tau, G, conv, eps)
+        v, dW, dG, _ = AD.flat_quantity_and_gradient(lat, steps, qq, pp, checkpoint_every=5)
+        lat.close()
+        assert abs(float(q[k].detach()) - v) <= 1e-13 * abs(v)
+        dW_sum = dW_sum + wts[k] * dW
+        dG_sum = dG_sum + wts[k] * dG
+    assert _rel(W.grad.numpy(), dW_sum) < 1e-12
+    assert abs(float(Gt.grad) - dG_sum) < 1e-12 * abs(dG_sum)
+    # sigma_0 of the device seed against the pinned lattice-summed sigma
     lat = _lat(lattice, shape, st, tau, G, conv, eps)
-    sigma, dW, dG, _ = AD.sigma_and_gradient(lat, steps, checkpoint_every=steps)
+    sig_sum, dW_s, dG_s, _ = AD.sigma_and_gradient(lat, steps, checkpoint_every=steps)
     lat.close()
-    assert float(s.detach()) == sigma
-    assert np.allclose(W.grad.numpy(), 2.0 * dW, rtol=0, atol=0)
-    assert float(Gt.grad) == 2.0 * dG
+    lat = _lat(lattice, shape, st, tau, G, conv, eps)
+    sig, dW_q, dG_q, _ = AD.flat_quantity_and_gradient(lat, steps, AD.LB_FLAT_SIGMA)
+    lat.close()
+    assert abs(sig * ny - sig_sum) < 1e-12 * abs(sig_sum)
+    assert _rel(dW_q * ny, dW_s) < 1e-10 and abs(dG_q * ny - dG_s) < 1e-10 * abs(dG_s)
 
 
 def test_gradient_solve_hits_target_sigma():
@@ -190,12 +212,12 @@ def test_density_functionals_match_oracle_adjoint(which):
     lattice, shape, st, tau, G, conv, eps, steps = CASES[0]
     nx, ny = shape
     if which == "ratio":
-        fn_gpu, fn_or = AD.density_ratio(nx // 2, 1), _oracle_ratio(nx // 2, 1)
+        spec, fn_or = AD.density_ratio(nx // 2, 1), _oracle_ratio(nx // 2, 1)
     else:
-        fn_gpu, fn_or = AD.interface_width(N_LIQ, N_GAS), _oracle_width(N_LIQ, N_GAS)
+        spec, fn_or = AD.interface_width(N_LIQ, N_GAS), _oracle_width(N_LIQ, N_GAS)
     lat = _lat(lattice, shape, st, tau, G, conv, eps)
     g0 = lat.state()
-    val, dW, dG, lam0 = AD.density_functional_and_gradient(lat, steps, fn_gpu, checkpoint_every=5)
+    val, dW, dG, lam0 = AD.flat_quantity_and_gradient(lat, steps, *spec, checkpoint_every=5)
     lat.close()
     o = oracle.Oracle(lattice, (1, ny, nx), st.groups, tau=tau, G=G, convention=conv)
     v_o, lam_o, dW_o, dGp_o = OAD.gradient_of_density_functional(o, g0.reshape((9, 1, ny, nx)), steps,
@@ -208,9 +230,10 @@ def test_density_functionals_match_oracle_adjoint(which):
 def test_interface_width_gradient_matches_gpu_finite_differences():
     lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
     steps = 150
-    fn = AD.interface_width(N_LIQ, N_GAS)
+    fn = _oracle_width(N_LIQ, N_GAS)
     lat = _lat(lattice, shape, st, tau, G, conv, eps)
-    w, dW, dG, _ = AD.density_functional_and_gradient(lat, steps, fn, checkpoint_every=40)
+    w, dW, dG, _ = AD.flat_quantity_and_gradient(lat, steps, *AD.interface_width(N_LIQ, N_GAS),
+                                                 checkpoint_every=40)
     lat.close()
     assert 1.0 < w < 10.0
 
