@@ -742,28 +742,55 @@ def run_gb300(args, dist, rank, ws):
         for l in lats:
             l.close()
 
-    # adjoint: gradients of sigma_0 through the step (D2Q9 E8, 512^2 periodic
-    # box holding a flat slab, FP32 forward, binary64 adjoint, checkpoint every
-    # 100 steps): forward with checkpoints, then every segment recomputed and
-    # carried back; adjoint steps per second of the whole procedure
+    # adjoint tuning as configured: D2Q9 E8, a flat 512 x 4 slab (binary32
+    # forward, 4,000 steps, checkpoint every 100, binary64 adjoint); Newton
+    # steps on the five group weights and G take (sigma_0, delta) to 1.2 x and
+    # 0.5 x their untuned values at fixed interface width and density ratio;
+    # the companion 512^2 droplet (R = 64) before and after, measured after
+    # 40,000 steps (at 4,000 its Laplace pressure is a third of equilibrium)
     adjoint = None
     if not args.no_adjoint:
         import paper_2505_23647_gb300.adjoint as PA
-        na, ka, ca = 512, 400, 100
-        rho_a = L.tanh_slab(na, na, 1, na // 4, 3 * na // 4, 0.456, 2.25, 2.0)
-        lat_a = P.Lattice("D2Q9", (na, na), rho_a, L.E8_2D.bases, L.E8_2D.weights, precision="fp32",
-                          tau=1.0, G=-3.0, convention="literal", stream=stream.cuda_stream)
+        ng3, nl3 = COEX_GP3
+        na, ka, ca = 512, 4000, 100
+
+        def c5_slab(W, G_):
+            rho_s = L.tanh_slab(na, 4, 1, na // 4, 3 * na // 4, ng3, nl3, 2.0)
+            return P.Lattice("D2Q9", (na, 4), rho_s, L.E8_2D.bases, W, precision="fp32",
+                             tau=1.0, G=G_, convention="literal", stream=stream.cuda_stream)
+
+        def c5_drop(W, G_):
+            rho_d = L.tanh_sphere(na, na, 1, 64.0, nl3, ng3, 2.0, center=(na / 2.0, na / 2.0, 0.0))
+            latd = P.Lattice("D2Q9", (na, na), rho_d, L.E8_2D.bases, W, precision="fp32",
+                             tau=1.0, G=G_, convention="literal", stream=stream.cuda_stream)
+            latd.step(40000)
+            okd = latd.sync() == P.LB_OK
+            r = latd.curved_interface((na / 2.0, na / 2.0)) if okd else {"stable": False}
+            latd.close()
+            return r
+
+        w0 = np.array([float(w) for w in L.E8_2D.weights])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sig, dWa, dGa, _ = PA.sigma_and_gradient(lat_a, ka, checkpoint_every=ca)
+        v0, _, _ = PA.slab_observables(lambda: c5_slab(list(w0), -3.0), ka, na // 2, 0, nl3, ng3, ca)
+        targets = v0 * np.array([1.2, 0.5, 1.0, 1.0])
+        wt, Gt, vals, hist = PA.tune_slab(c5_slab, lambda k: [float(v) for v in k], w0, -3.0, targets,
+                                          ka, na // 2, 0, nl3, ng3, ca, rtol=1e-3, max_iter=12)
         torch.cuda.synchronize()
         dta = reduce_max(dist, time.perf_counter() - t0, dev)
-        lat_a.close()
-        adjoint = {"value": ka / dta, "unit": "adjoint steps/s", "lattice": f"D2Q9 E8 {na}x{na} slab",
-                   "steps": ka, "checkpoint_every": ca, "seconds": dta,
-                   "mlups": na * na * ka / dta / 1e6, "precision": "fp32 forward, binary64 adjoint",
-                   "sigma": sig, "dsigma_dG": dGa,
-                   "accuracy": "FP32-forward gradient within 1e-3 of FP64 (tests/test_gpu_adjoint.py)"}
+        sweeps = 4 * (len(hist) + 1)      # adjoint sweeps of ka steps (4 quantities per Jacobian)
+        d0, d1 = c5_drop(list(w0), -3.0), c5_drop(list(wt), float(Gt))
+        adjoint = {"value": sweeps * ka / dta, "unit": "adjoint steps/s (whole solve)",
+                   "lattice": f"D2Q9 E8 {na}x4 slab, binary32 forward, binary64 adjoint",
+                   "steps": ka, "checkpoint_every": ca, "newton_iterations": len(hist),
+                   "seconds": dta, "untuned": {"sigma0": v0[0], "delta": v0[1], "width": v0[2],
+                                               "ratio": v0[3]},
+                   "targets": list(targets), "achieved": list(vals),
+                   "max_rel_error": float(np.max(np.abs(vals / targets - 1.0))),
+                   "weights": {"untuned": list(w0), "tuned": [float(v) for v in wt], "G": float(Gt)},
+                   "droplet_512_R64_40000_steps": {"untuned": d0, "tuned": d1},
+                   "accuracy": "gradients vs central differences and the binary64 oracle adjoint: "
+                               "tests/test_gpu_adjoint.py; this solve: tests/test_gpu_c5.py"}
 
     # end to end through the C ABI with host buffers: create from the pinned
     # host density (H2D), K steps, read back the density (D2H) and the
