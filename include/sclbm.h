@@ -214,10 +214,17 @@ lb_status lb_sync(lb_ctx *ctx);
  * with binary64 warp-shuffle reductions (compensated double-double sums in a
  * fixed order, rounded once): mass, momentum sum(j + F/2), max |u|, min/max
  * n.  Binary64 lattices: every node quantity in binary64.  Shifted-binary32
- * lattices: n from the widened populations (to 2^-47 relative), F, u and
- * j + F/2 in binary32 (the step's precision), the sums in binary64.
- * Synchronous; allocates nothing.  Returns LB_EUNSTABLE (with *out filled)
- * if a density check failed. */
+ * lattices: the mass from each node's widened density (to 2^-47 relative),
+ * F, u and j + F/2 in binary32 (the step's precision), the sums in binary64.
+ * Shifted-binary32 D3Q19 lattices on the TMA step kernel are measured by
+ * that kernel's measuring instantiation (one read of the populations, psi
+ * never stored; the node sums compensated in binary32 pairs before the
+ * binary64 reduction; min/max n are the step's binary32 densities); the
+ * others by a generic pass that reads psi from a halo'd copy (min/max n
+ * widened).  Synchronous; allocates nothing (the per-block records go to
+ * the idle population buffer or the context's reduction buffer).  Returns
+ * LB_EUNSTABLE (with *out filled) if a density check failed, LB_ECUDA if a
+ * bounded wait of the measuring pass gave up. */
 lb_status lb_observables(lb_ctx *ctx, lb_obs *out);
 
 /* Lattice pressure tensor (Appendices E and F) including the ideal part

@@ -544,6 +544,7 @@ lb_status lb_set_stencil(lb_ctx *c, int n_groups, const int *base_vectors, const
         F.pull_pad = c->g.ox > 0 && c->g.oy > 0;
         for (size_t a = 0; a < vec.size(); ++a) {
             F.nb[a] = (vec[a][2] * F.pyp + vec[a][1]) * F.pxp + vec[a][0];
+            F.nbs[a] = (vec[a][2] * ct_by(c->D) + vec[a][1]) * CT_BX + vec[a][0];
             for (int k = 0; k < 3; ++k) F.we[a][k] = (float)(w[a] * (double)vec[a][k]);
         }
         for (int i = 0; i < c->Q; ++i) {

@@ -49,14 +49,19 @@ cudaError_t f32_step(lb_ctx *c) {
         k_psi_f32<2, 9><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->pfast, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
-        k_collide_f32<2, 9><<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pfast, k, c->flags);
+        const dim3 grid((c->g.nx + CT_X - 1) / CT_X, (c->g.ny + CT_Y2 - 1) / CT_Y2, 1);
+        k_collide_f32<2, 9><<<grid, dim3(CT_X, CT_Y), ct_box(2) * sizeof(float), c->stream>>>(
+            A, B, psi, c->g, c->pfast, k, c->flags);
         tm_end(c);
     } else {
         tm_begin(c, LB_KERNEL_PSI);
         k_psi_f32<3, 19><<<gb, 256, 0, c->stream>>>(A, psi, c->g, k.rho0, c->pfast, c->flags, psik(c));
         tm_end(c);
         tm_begin(c, LB_KERNEL_COLLIDE);
-        k_collide_f32<3, 19><<<gb, 256, 0, c->stream>>>(A, B, psi, c->g, c->pfast, k, c->flags);
+        const dim3 grid((c->g.nx + CT_X - 1) / CT_X, (c->g.ny + CT_Y - 1) / CT_Y,
+                        (c->g.nz + CT_Z - 1) / CT_Z);
+        k_collide_f32<3, 19><<<grid, dim3(CT_X, CT_Y), ct_box(3) * sizeof(float), c->stream>>>(
+            A, B, psi, c->g, c->pfast, k, c->flags);
         tm_end(c);
     }
     c->launches += 2;

@@ -127,7 +127,17 @@ __device__ __forceinline__ void issue_plane(const CUtensorMap *map, float *stage
 //   store it.
 // The psi plane (it & 1) is rewritten at it + 2, after every thread has
 // passed the barrier of it + 1, i.e. finished reading it.
-template <int R, int NG, bool EPS, bool F2>
+//
+// MEAS: the measuring instantiation.  The same march over the current state,
+// but instead of colliding and storing, each node adds its widened density
+// (the binary32 sum of its populations plus that sum's rounding errors), its
+// j + F/2 and |u|^2 (formed as collide19 forms them) and its binary32 density
+// to per-thread compensated sums and extrema; each block writes one MeasRec
+// (binary32 pairs, shifted densities) to B[block].  Nothing else is written
+// and the step counter does not move.  (Binary32 pairs, not binary64: this
+// GPU's binary64 rate is a small fraction of its binary32 rate, and a
+// binary64 tree over every block took longer than the march.)
+template <int R, int NG, bool EPS, bool F2, bool MEAS>
 __global__ void __launch_bounds__(TX * TY, 2)
     k_fused3d_tma(const __grid_constant__ CUtensorMap map, float *__restrict__ B, const Params p,
                   Flags *flags) {
@@ -178,6 +188,10 @@ __global__ void __launch_bounds__(TX * TY, 2)
 #pragma unroll
     for (int k = 0; k <= 2 * R; ++k) acc[k][0] = acc[k][1] = acc[k][2] = ps[k] = 0.f;
     bool timed_out = false;
+    // MEAS only: compensated sums (value, error) of the shifted density and
+    // of j + F/2; the largest |u|^2; the density extrema
+    float sm = 0.f, em = 0.f, sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f, sz = 0.f, ez = 0.f;
+    float uu_max = 0.f, n_lo = __int_as_float(0x7f800000), n_hi = -__int_as_float(0x7f800000);
 
     // unrolled by 2: the stage and psi-plane parity (it & 1) becomes a
     // compile-time constant in each copy (measured 0.8-1.3 % faster; by 4 the
@@ -246,9 +260,26 @@ __global__ void __launch_bounds__(TX * TY, 2)
             F[0] = pre * acc[0][0];
             F[1] = pre * acc[0][1];
             F[2] = pre * fz;
-            float out[19];
-            collide19<F2>(gq[CS], dq[CS], F, p, out);
-            store19(B, p, xi, yi, z0 - 2 * R + it, out);
+            if constexpr (MEAS) {
+                float m[3], uu;
+                moments19(gq[CS], dq[CS], F, p, m, uu);
+                float s = gq[CS][0], e = 0.f;
+#pragma unroll
+                for (int i = 1; i < 19; ++i) ff_acc(s, e, gq[CS][i]);
+                ff_acc(sm, em, s);
+                em += e;
+                ff_acc(sx, ex, m[0]);
+                ff_acc(sy, ey, m[1]);
+                ff_acc(sz, ez, m[2]);
+                uu_max = fmaxf(uu_max, uu);
+                const float n = dq[CS] + p.rho0;
+                n_lo = fminf(n_lo, n);
+                n_hi = fmaxf(n_hi, n);
+            } else {
+                float out[19];
+                collide19<F2>(gq[CS], dq[CS], F, p, out);
+                store19(B, p, xi, yi, z0 - 2 * R + it, out);
+            }
         }
         // advance the force and psi windows by one plane
 #pragma unroll
@@ -278,11 +309,41 @@ __global__ void __launch_bounds__(TX * TY, 2)
             for (; seen1 < issued1; ++seen1)
                 mbar_wait_bounded(&bar[1], (unsigned)seen1 & 1u, MAX_POLLS);
         }
-        finish_step(flags, t);
+        if constexpr (MEAS) {
+            if (t == 0) {   // a NaN mass marks the measurement as failed
+                MeasRec r = meas_zero();
+                r.v[0] = __int_as_float(0x7fc00000);
+                reinterpret_cast<MeasRec *>(B)[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = r;
+            }
+        } else {
+            finish_step(flags, t);
+        }
         return;
     }
-    if (bad) atomicMin(&flags->err_step, flags->step);
-    finish_step(flags, t);
+    if constexpr (MEAS) {
+        // the block's record: warp trees, then the 8 warps' records in warp 0
+        MeasRec r;
+        meas_pair(r, 0, sm, em);
+        meas_pair(r, 2, sx, ex);
+        meas_pair(r, 4, sy, ey);
+        meas_pair(r, 6, sz, ez);
+        r.v[8] = uu_max;
+        r.v[9] = n_lo;
+        r.v[10] = n_hi;
+        meas_warp(r);
+        __shared__ MeasRec wred[TX * TY / 32];
+        if ((t & 31) == 0) wred[t >> 5] = r;
+        __syncthreads();
+        if (t < 32) {
+            r = t < TX * TY / 32 ? wred[t] : meas_zero();
+            meas_warp(r);
+            if (t == 0)
+                reinterpret_cast<MeasRec *>(B)[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = r;
+        }
+    } else {
+        if (bad) atomicMin(&flags->err_step, flags->step);
+        finish_step(flags, t);
+    }
 }
 
 template <int R>
@@ -290,34 +351,34 @@ constexpr int smem_bytes() {
     return (2 * 19 * box_stride<R>() + 2 * (TX + 2 * R) * (TY + 2 * R)) * 4 + 16;
 }
 
-template <int R, int NG, bool EPS, bool F2>
+template <int R, int NG, bool EPS, bool F2, bool MEAS>
 void launch1(dim3 grid, dim3 block, const CUtensorMap &map, float *B, const Params &p, lb_ctx *c) {
     static std::atomic<unsigned long long> attr_done{0};   // devices done, one bit each
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = 1ULL << (dev & 63);
     if (!(attr_done.load() & bit)) {
-        cudaFuncSetAttribute(k_fused3d_tma<R, NG, EPS, F2>,
+        cudaFuncSetAttribute(k_fused3d_tma<R, NG, EPS, F2, MEAS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<R>());
         attr_done.fetch_or(bit);
     }
-    k_fused3d_tma<R, NG, EPS, F2><<<grid, block, smem_bytes<R>(), c->stream>>>(map, B, p, c->flags);
+    k_fused3d_tma<R, NG, EPS, F2, MEAS><<<grid, block, smem_bytes<R>(), c->stream>>>(map, B, p, c->flags);
 }
 
-// the instantiation for the stencil's widest group (ng = 1..7), the psi kind
-// and the forcing variant; m1, m2: the tensor maps with boxes of TY + 2 and
-// TY + 4 rows
-template <bool EPS, bool F2>
+// the instantiation for the stencil's widest group (ng = 1..7), the psi kind,
+// the forcing variant and step or measurement; m1, m2: the tensor maps with
+// boxes of TY + 2 and TY + 4 rows
+template <bool EPS, bool F2, bool MEAS = false>
 void launch(int ng, dim3 grid, dim3 block, const CUtensorMap &m1, const CUtensorMap &m2, float *B,
             const Params &p, lb_ctx *c) {
     switch (ng) {
-        case 1: launch1<1, 1, EPS, F2>(grid, block, m1, B, p, c); break;
-        case 2: launch1<1, 2, EPS, F2>(grid, block, m1, B, p, c); break;
-        case 3: launch1<1, 3, EPS, F2>(grid, block, m1, B, p, c); break;
-        case 4: launch1<2, 4, EPS, F2>(grid, block, m2, B, p, c); break;
-        case 5: launch1<2, 5, EPS, F2>(grid, block, m2, B, p, c); break;
-        case 6: launch1<2, 6, EPS, F2>(grid, block, m2, B, p, c); break;
-        default: launch1<2, 7, EPS, F2>(grid, block, m2, B, p, c); break;
+        case 1: launch1<1, 1, EPS, F2, MEAS>(grid, block, m1, B, p, c); break;
+        case 2: launch1<1, 2, EPS, F2, MEAS>(grid, block, m1, B, p, c); break;
+        case 3: launch1<1, 3, EPS, F2, MEAS>(grid, block, m1, B, p, c); break;
+        case 4: launch1<2, 4, EPS, F2, MEAS>(grid, block, m2, B, p, c); break;
+        case 5: launch1<2, 5, EPS, F2, MEAS>(grid, block, m2, B, p, c); break;
+        case 6: launch1<2, 6, EPS, F2, MEAS>(grid, block, m2, B, p, c); break;
+        default: launch1<2, 7, EPS, F2, MEAS>(grid, block, m2, B, p, c); break;
     }
 }
 
@@ -376,6 +437,51 @@ cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng) {
     tm_end(c);
     c->launches += 1;
     c->cur = 1 - c->cur;
+    return cudaGetLastError();
+}
+
+// All blocks' records in one block, then the observables in binary64 (the
+// layout of the generic pass's results): mass (plus N rho0), momentum,
+// max |u|, min n, max n.
+__global__ void __launch_bounds__(256) k_meas_final(int nb, const fc::MeasRec *__restrict__ part,
+                                                    double *out, double mass_add) {
+    fc::MeasRec r = fc::meas_zero();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) fc::meas_combine(r, part[b]);
+    fc::meas_warp(r);
+    __shared__ fc::MeasRec wred[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) wred[w] = r;
+    __syncthreads();
+    if (w == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? wred[lane] : fc::meas_zero();
+        fc::meas_warp(r);
+        if (lane == 0) {
+            out[0] = ((double)r.v[0] + mass_add) + (double)r.v[1];
+            for (int k = 0; k < 3; ++k) out[1 + k] = (double)r.v[2 + 2 * k] + (double)r.v[3 + 2 * k];
+            out[4] = sqrt((double)r.v[8]);
+            out[5] = (double)r.v[9];
+            out[6] = (double)r.v[10];
+        }
+    }
+}
+
+// The measuring pass over the current state (the MEAS instantiation; the
+// forcing variant does not change n, j + F/2 or u): one record per block
+// into part, then k_meas_final into res (7 doubles).
+cudaError_t f32_fused3d_tma_measure(lb_ctx *c, void *part, double *res) {
+    fc::Params p = fused_params(c, c->fused_W);
+    dim3 block(fc::TX, fc::TY);
+    dim3 grid(c->g.nx / fc::TX, c->g.ny / fc::TY, (c->g.nz + p.zchunk - 1) / p.zchunk);
+    const CUtensorMap &m1 = c->tmap[c->cur][0], &m2 = c->tmap[c->cur][1];
+    float *out = (float *)part;
+    if (p.inv_eps != 0.f)
+        ft::launch<true, false, true>(c->fused_ng, grid, block, m1, m2, out, p, c);
+    else
+        ft::launch<false, false, true>(c->fused_ng, grid, block, m1, m2, out, p, c);
+    const int nb = (int)(grid.x * grid.y * grid.z);
+    const double add = (double)c->g.N * (double)p.rho0;
+    k_meas_final<<<1, 256, 0, c->stream>>>(nb, (const fc::MeasRec *)part, res, add);
+    c->launches += 2;
     return cudaGetLastError();
 }
 

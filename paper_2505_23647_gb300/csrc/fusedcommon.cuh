@@ -245,6 +245,85 @@ __device__ __forceinline__ void collide19(const float *g, float dn, const float 
 #undef SCLBM_PAIR
 }
 
+// A node's j + F/2 and |u|^2 formed exactly as collide19 forms them (the
+// same operations in the same order), for the fused kernel's measuring
+// instantiation.
+__device__ __forceinline__ void moments19(const float *g, float dn, const float *F,
+                                          const Params &p, float *m, float &uu) {
+    const float n = dn + p.rho0;
+    const float inv = __frcp_rn(n);
+    const float d1 = g[1] - g[2], d3 = g[3] - g[4], d5 = g[5] - g[6];
+    const float d7 = g[7] - g[8], d9 = g[9] - g[10], d11 = g[11] - g[12];
+    const float d13 = g[13] - g[14], d15 = g[15] - g[16], d17 = g[17] - g[18];
+    const float jx = ((d1 + d7) + (d9 + d11)) + d13;
+    const float jy = ((d3 + d7) + (d15 - d9)) + d17;
+    const float jz = ((d5 + d11) + (d15 - d13)) - d17;
+    m[0] = fmaf(0.5f, F[0], jx);
+    m[1] = fmaf(0.5f, F[1], jy);
+    m[2] = fmaf(0.5f, F[2], jz);
+    const float ux = m[0] * inv, uy = m[1] * inv, uz = m[2] * inv;
+    uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+}
+
+// (s, e) += v with the rounding error kept (two_sum); s + e carries the
+// running sum to about 2^-48 relative
+__device__ __forceinline__ void ff_acc(float &s, float &e, float v) {
+    const float t = s + v;
+    const float bb = t - s;
+    e += (s - (t - bb)) + (v - bb);
+    s = t;
+}
+
+// Observables record of the fused kernel's measuring pass, in binary32
+// pairs (value, error): v[0..1] shifted mass, v[2..7] momentum x, y, z;
+// v[8] max |u|^2, v[9] min n, v[10] max n.
+struct MeasRec {
+    float v[11];
+};
+
+__device__ __forceinline__ MeasRec meas_zero() {
+    MeasRec r;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r.v[k] = 0.f;
+    r.v[8] = 0.f;
+    r.v[9] = __int_as_float(0x7f800000);
+    r.v[10] = -__int_as_float(0x7f800000);
+    return r;
+}
+
+// (hi, lo) normalised from a value and its error
+__device__ __forceinline__ void meas_pair(MeasRec &r, int k, float s, float e) {
+    const float t = s + e;
+    r.v[k] = t;
+    r.v[k + 1] = e - (t - s);
+}
+
+// r += o: pairs added with their rounding errors kept (two_sum, then the
+// errors and a renormalisation), extrema combined
+__device__ __forceinline__ void meas_combine(MeasRec &r, const MeasRec &o) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        const float s = r.v[k] + o.v[k];
+        const float bb = s - r.v[k];
+        const float err = (r.v[k] - (s - bb)) + (o.v[k] - bb);
+        meas_pair(r, k, s, err + (r.v[k + 1] + o.v[k + 1]));
+    }
+    r.v[8] = fmaxf(r.v[8], o.v[8]);
+    r.v[9] = fminf(r.v[9], o.v[9]);
+    r.v[10] = fmaxf(r.v[10], o.v[10]);
+}
+
+// a warp's records combined by xor-shuffles (every lane ends with the sum)
+__device__ __forceinline__ void meas_warp(MeasRec &r) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        MeasRec o;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) o.v[k] = __shfl_xor_sync(0xffffffffu, r.v[k], off);
+        meas_combine(r, o);
+    }
+}
+
 // columns next to each x edge written again as periodic images: a plane box
 // reads 4 of them; 8 make each image one whole 32-byte sector of the row
 // (measured 0.537 -> 0.520 ms per 256^3 step against 4)

@@ -34,6 +34,7 @@ struct PairsF32 {
 struct PairsFast {
     int npairs, R;
     int nb[MAXP];         // offsets of e_a in the halo'd psi field
+    int nbs[MAXP];        // offsets of e_a in a collision tile's psi box
     float we[MAXP][3];
     int pop[19];
     int H, Hz;            // psi halo in x, y and in z (0 in 2D)
@@ -43,6 +44,14 @@ struct PairsFast {
 // binary32 psi fields of the generic kernels carry a periodic halo of
 // PSI_HALO nodes on every side (x, y and, in 3D, z)
 constexpr int PSI_HALO = LB_MAX_RADIUS;
+// Tile of the generic binary32 collision (k_collide_f32): 32 x 8 threads
+// take a brick of 32 x 8 x 8 nodes (3D) or 32 x 32 nodes (2D, four rows a
+// thread); the brick's psi box carries a PSI_HALO halo on every side.
+constexpr int CT_X = 32, CT_Y = 8, CT_Z = 8, CT_Y2 = 32;
+constexpr int CT_BX = CT_X + 2 * PSI_HALO;
+constexpr int ct_by(int D) { return (D == 3 ? CT_Y : CT_Y2) + 2 * PSI_HALO; }
+constexpr int ct_bz(int D) { return D == 3 ? CT_Z + 2 * PSI_HALO : 1; }
+constexpr int ct_box(int D) { return CT_BX * ct_by(D) * ct_bz(D); }
 
 // Per-context constants of the collision (formed on the host once, in the
 // same expressions as the reference: omega = 1/tau, cw_i = (1 - 1/(2 tau)) w_i).
@@ -214,6 +223,9 @@ cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi);
 bool fused3d_applicable(const lb_ctx *c, float *W, int *ng);
 cudaError_t f32_fused3d_step(lb_ctx *c, const float *W, int ng);
 cudaError_t f32_fused3d_tma_step(lb_ctx *c, const float *W, int ng);
+// the fused TMA kernel's measuring pass: per-block records staged in part,
+// the 7 observables (binary64, the generic pass's layout) into res
+cudaError_t f32_fused3d_tma_measure(lb_ctx *c, void *part, double *res);
 bool tma_make_maps(lb_ctx *c);
 // fused single-pass D2Q9 step (batch2d.cu)
 bool fused2d_applicable(const lb_ctx *c, float *W5);

@@ -347,33 +347,93 @@ __global__ void __launch_bounds__(256) k_psi_f32(const float *__restrict__ A, fl
     }
 }
 
+// The generic binary32 collision.  A block of CT_X x CT_Y threads takes one
+// brick (CT_X x CT_Y x CT_Z nodes in 3D, CT_X x CT_Y2 in 2D); the brick's
+// psi box (PSI_HALO more on every side) is read from the halo'd field into
+// shared memory once.  Each thread first forms the force sums of all its
+// nodes (a column of NPT nodes), pair by pair, so that a pair's offset and
+// folded weights are read once for NPT nodes; per node the operations are
+// those of force_fast in the same order, so the result is bit for bit the
+// one the global-memory form gives.  Then it pulls, collides and stores its
+// nodes one by one.  Requires the halo'd psi field (fewer than 2^31 of its
+// nodes) and dynamic shared memory of ct_box(D) floats.
 template <int D, int Q>
-__global__ void __launch_bounds__(256) k_collide_f32(const float *__restrict__ A, float *__restrict__ B,
+__global__ void __launch_bounds__(CT_X * CT_Y) k_collide_f32(const float *__restrict__ A, float *__restrict__ B,
                                                      const float *__restrict__ psi, Geom g,
                                                      const PairsFast PF, const ConstsT<float> k,
                                                      Flags *flags) {
-    const int N = (int)g.N, stride = gridDim.x * blockDim.x;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += stride) {
-        int x, y, z;
-        coords32(g, s, x, y, z);
+    extern __shared__ __align__(16) float sps[];
+    constexpr int BX = CT_BX, BY = ct_by(D), BZ = ct_bz(D);
+    constexpr int NPT = D == 3 ? CT_Z : CT_Y2 / CT_Y;   // nodes a thread takes
+    // shared-memory distance between a thread's consecutive nodes
+    constexpr int STEP = D == 3 ? BX * BY : CT_Y * BX;
+    const int x0 = blockIdx.x * CT_X, y0 = blockIdx.y * (D == 3 ? CT_Y : CT_Y2);
+    const int z0 = D == 3 ? blockIdx.z * CT_Z : 0;
+    const int t = threadIdx.y * CT_X + threadIdx.x;
+    // the box's origin in the halo'd field is node (x0 - H, y0 - H, z0 - Hz):
+    // BY * BZ rows of BX floats from row (z0 + bz) * pyp + y0 + by, column x0
+    const int fz_end = g.nz + 2 * PF.Hz;
+    if ((PF.pxp & 3) == 0) {   // rows start on 16 bytes: float4 copies
+        constexpr int V = BX / 4;
+        for (int e = t; e < V * BY * BZ; e += CT_X * CT_Y) {
+            const int r = e / V, q = e - r * V;
+            const int by = r % BY, bz = r / BY;
+            const int fx = x0 + 4 * q, fy = y0 + by, fz = z0 + bz;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (fx < PF.pxp && fy < PF.pyp && fz < fz_end)
+                v = *reinterpret_cast<const float4 *>(psi + (fz * PF.pyp + fy) * PF.pxp + fx);
+            reinterpret_cast<float4 *>(sps)[e] = v;
+        }
+    } else {
+        for (int e = t; e < BX * BY * BZ; e += CT_X * CT_Y) {
+            const int bx = e % BX, r = e / BX, by = r % BY, bz = r / BY;
+            const int fx = x0 + bx, fy = y0 + by, fz = z0 + bz;
+            float v = 0.f;
+            if (fx < PF.pxp && fy < PF.pyp && fz < fz_end) v = psi[(fz * PF.pyp + fy) * PF.pxp + fx];
+            sps[e] = v;
+        }
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    // smem index of the thread's first node
+    const int c0 = (PF.Hz * BY + threadIdx.y + PF.H) * BX + threadIdx.x + PF.H;
+    float acc[NPT][3];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = 0.f;
+#pragma unroll 2
+    for (int a = 0; a < PF.npairs; ++a) {
+        const int o = PF.nbs[a];
+        const float w0 = PF.we[a][0], w1 = PF.we[a][1], w2 = PF.we[a][2];
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const float d = sps[c0 + j * STEP + o] - sps[c0 + j * STEP - o];
+            acc[j][0] = fmaf(w0, d, acc[j][0]);
+            acc[j][1] = fmaf(w1, d, acc[j][1]);
+            if (D == 3) acc[j][2] = fmaf(w2, d, acc[j][2]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int y = D == 3 ? y0 + threadIdx.y : y0 + threadIdx.y + CT_Y * j;
+        const int z = D == 3 ? z0 + j : 0;
+        if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
         float fi[Q];
         pull_f32<D, Q>(A, g, x, y, z, PF, fi);
         const float dn = sum_q<float, Q>(fi);
         const float n = dn + k.rho0;
-        const int sp = psi_at(PF, x, y, z);
-        float acc[3];
-        force_fast<D>(psi, sp, PF, acc);
-        const float pre = k.mGp * psi[sp];
+        const float pre = k.mGp * sps[c0 + j * STEP];
         float F[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int mu = 0; mu < D; ++mu) F[mu] = pre * acc[mu];
+        F[0] = pre * acc[j][0];
+        F[1] = pre * acc[j][1];
+        if (D == 3) F[2] = pre * acc[j][2];
         float fo[Q];
         collide<float, D, Q, true>(fi, n, dn, F, k, fo, nullptr, nullptr);
         const long long ps = ((long long)z * g.nyp + (y + g.oy)) * g.nxp + (x + g.ox);
 #pragma unroll
         for (int i = 0; i < Q; ++i) B[(long long)i * g.Np + ps] = fo[i];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) flags->step = flags->step + 1;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0)
+        flags->step = flags->step + 1;
 }
 
 // Density and psi in binary64 from a state of either precision.
@@ -510,6 +570,49 @@ __global__ void k_ghosts(T *__restrict__ A, Geom g, int Q) {
                               (wrapi(xl, g.nx) + g.ox);
         A[k] = A[src];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Observables reduced in binary64: compensated (double-double) sums in a
+// fixed order (the generic observables pass and the fused step kernel's
+// measuring instantiation both produce one record per block)
+struct Red {
+    ddv mass, mom[3];
+    double umax2, rmin, rmax;
+};
+
+__device__ __forceinline__ Red red_zero() {
+    Red r;
+    r.mass = {0.0, 0.0};
+    for (int k = 0; k < 3; ++k) r.mom[k] = {0.0, 0.0};
+    r.umax2 = 0.0;
+    r.rmin = __longlong_as_double(0x7ff0000000000000ULL);
+    r.rmax = -__longlong_as_double(0x7ff0000000000000ULL);
+    return r;
+}
+
+__device__ __forceinline__ void red_combine(Red &a, const Red &b) {
+    a.mass = dd_add(a.mass, b.mass);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.mom[k] = dd_add(a.mom[k], b.mom[k]);
+    a.umax2 = fmax(a.umax2, b.umax2);
+    a.rmin = fmin(a.rmin, b.rmin);
+    a.rmax = fmax(a.rmax, b.rmax);
+}
+
+__device__ __forceinline__ Red red_shfl(const Red &r, int off) {
+    Red o;
+    o.mass.hi = __shfl_down_sync(0xffffffffu, r.mass.hi, off);
+    o.mass.lo = __shfl_down_sync(0xffffffffu, r.mass.lo, off);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o.mom[k].hi = __shfl_down_sync(0xffffffffu, r.mom[k].hi, off);
+        o.mom[k].lo = __shfl_down_sync(0xffffffffu, r.mom[k].lo, off);
+    }
+    o.umax2 = __shfl_down_sync(0xffffffffu, r.umax2, off);
+    o.rmin = __shfl_down_sync(0xffffffffu, r.rmin, off);
+    o.rmax = __shfl_down_sync(0xffffffffu, r.rmax, off);
+    return o;
 }
 
 inline int grid_for(long long N, int block = 256, int cap = 152 * 32) {

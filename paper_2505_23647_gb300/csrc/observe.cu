@@ -8,7 +8,9 @@
 //    every node quantity in binary64 (bit for bit the step's own values);
 //    shifted-binary32 lattices take F, u and j + F/2 in binary32 (the
 //    step's precision) and only the density, summed from the widened
-//    populations, and the global sums in binary64.
+//    populations, and the global sums in binary64.  Shifted-binary32 D3Q19
+//    lattices on the TMA step kernel are measured by that kernel's
+//    measuring instantiation (fused3d_tma.cu) instead of k_obs.
 //  * the lattice pressure tensor (Appendices E, F) in binary64, the density
 //    recomputed from the populations where it is needed;
 //  * flat interfaces (Sec. III B, Sec. IV): the profiles of n and of
@@ -34,47 +36,6 @@
 #include "kernels.cuh"
 
 namespace sclbm {
-
-// ---------------------------------------------------------------------------
-// binary64 reductions: compensated (double-double) sums in a fixed order
-struct Red {
-    ddv mass, mom[3];
-    double umax2, rmin, rmax;
-};
-
-__device__ __forceinline__ Red red_zero() {
-    Red r;
-    r.mass = {0.0, 0.0};
-    for (int k = 0; k < 3; ++k) r.mom[k] = {0.0, 0.0};
-    r.umax2 = 0.0;
-    r.rmin = __longlong_as_double(0x7ff0000000000000ULL);
-    r.rmax = -__longlong_as_double(0x7ff0000000000000ULL);
-    return r;
-}
-
-__device__ __forceinline__ void red_combine(Red &a, const Red &b) {
-    a.mass = dd_add(a.mass, b.mass);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a.mom[k] = dd_add(a.mom[k], b.mom[k]);
-    a.umax2 = fmax(a.umax2, b.umax2);
-    a.rmin = fmin(a.rmin, b.rmin);
-    a.rmax = fmax(a.rmax, b.rmax);
-}
-
-__device__ __forceinline__ Red red_shfl(const Red &r, int off) {
-    Red o;
-    o.mass.hi = __shfl_down_sync(0xffffffffu, r.mass.hi, off);
-    o.mass.lo = __shfl_down_sync(0xffffffffu, r.mass.lo, off);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        o.mom[k].hi = __shfl_down_sync(0xffffffffu, r.mom[k].hi, off);
-        o.mom[k].lo = __shfl_down_sync(0xffffffffu, r.mom[k].lo, off);
-    }
-    o.umax2 = __shfl_down_sync(0xffffffffu, r.umax2, off);
-    o.rmin = __shfl_down_sync(0xffffffffu, r.rmin, off);
-    o.rmax = __shfl_down_sync(0xffffffffu, r.rmax, off);
-    return o;
-}
 
 // warp tree, then the warps' results in one warp (block of 256 threads)
 __device__ __forceinline__ Red red_block(Red r) {
@@ -256,6 +217,13 @@ cudaError_t obs_fused(lb_ctx *c) {
     Red *part = reinterpret_cast<Red *>(c->red);
     double *res = obs_results(c);
     int gb = grid_for(c->g.N);
+    if (c->p.precision != LB_FP64 && c->Q == 19 && c->fast3d_ok && c->fused_enabled &&
+        c->tma_ok && c->fused_tma) {
+        // the fused step kernel's measuring pass: one read of the populations,
+        // the force from psi planes in registers; its per-block records go
+        // to the idle population buffer
+        return f32_fused3d_tma_measure(c, c->f[1 - c->cur], res);
+    }
     const ObsOff off = obs_offsets(c);
     if (c->p.precision == LB_FP64) {
         const double *A = (const double *)c->f[c->cur];
