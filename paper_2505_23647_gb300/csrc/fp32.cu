@@ -67,7 +67,8 @@ cudaError_t f32_step(lb_ctx *c) {
     c->launches += 2;
     c->cur = 1 - c->cur;
     cudaError_t e = cudaGetLastError();
-    return e != cudaSuccess ? e : ghosts_refresh(c);
+    // k_collide_f32 writes the ghost images itself; the wrapped kernels do not
+    return e != cudaSuccess || c->psi_halo ? e : ghosts_refresh(c);
 }
 
 cudaError_t f32_density_psi(lb_ctx *c, double *n, double *psi) {

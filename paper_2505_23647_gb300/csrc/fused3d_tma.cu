@@ -399,6 +399,10 @@ bool tma_make_maps(lb_ctx *c) {
             return false;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
+    // L2 fills promoted to 64 bytes only: a box row starts and ends inside a
+    // 128-byte line, and with 256-byte promotion every row edge also pulled
+    // the dead padding next to the ghost columns from DRAM (measured at
+    // 256^3: 1.74 -> 1.55 GB read per step, the step time unchanged)
     for (int b = 0; b < 2; ++b)
         for (int r = 0; r < 2; ++r) {
             // boxes of TY + 2R rows (R = 1, 2)
@@ -411,7 +415,7 @@ bool tma_make_maps(lb_ctx *c) {
             cuuint32_t es[3] = {1, 1, 1};
             CUresult res = encode(&c->tmap[b][r], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->f[b],
                                   dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (res != CUDA_SUCCESS) return false;
         }

@@ -324,10 +324,6 @@ __device__ __forceinline__ void meas_warp(MeasRec &r) {
     }
 }
 
-// columns next to each x edge written again as periodic images: a plane box
-// reads 4 of them; 8 make each image one whole 32-byte sector of the row
-// (measured 0.537 -> 0.520 ms per 256^3 step against 4)
-constexpr int GHOST_X = 8;
 
 // Write a node's 19 post-collision populations; on a padded layout also its
 // periodic images in the ghost columns (x < 8, x >= nx-8) and rows (y < 3,

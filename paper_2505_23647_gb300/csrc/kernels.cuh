@@ -355,8 +355,10 @@ __global__ void __launch_bounds__(256) k_psi_f32(const float *__restrict__ A, fl
 // folded weights are read once for NPT nodes; per node the operations are
 // those of force_fast in the same order, so the result is bit for bit the
 // one the global-memory form gives.  Then it pulls, collides and stores its
-// nodes one by one.  Requires the halo'd psi field (fewer than 2^31 of its
-// nodes) and dynamic shared memory of ct_box(D) floats.
+// nodes one by one, with their periodic images on a padded layout (as the
+// fused kernels write them), so no separate ghost refresh follows the step.
+// Requires the halo'd psi field (fewer than 2^31 of its nodes) and dynamic
+// shared memory of ct_box(D) floats.
 template <int D, int Q>
 __global__ void __launch_bounds__(CT_X * CT_Y) k_collide_f32(const float *__restrict__ A, float *__restrict__ B,
                                                      const float *__restrict__ psi, Geom g,
@@ -412,10 +414,20 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_collide_f32(const float *__rest
             if (D == 3) acc[j][2] = fmaf(w2, d, acc[j][2]);
         }
     }
-#pragma unroll
+    // the node loop is not unrolled (one copy of the pull, collision and
+    // stores); acc[0] always holds the current node's sums, shifted down
+    // after each node
+#pragma unroll 1
     for (int j = 0; j < NPT; ++j) {
         const int y = D == 3 ? y0 + threadIdx.y : y0 + threadIdx.y + CT_Y * j;
         const int z = D == 3 ? z0 + j : 0;
+        const float s0 = acc[0][0], s1 = acc[0][1], s2 = acc[0][2];
+#pragma unroll
+        for (int q = 0; q + 1 < NPT; ++q) {
+            acc[q][0] = acc[q + 1][0];
+            acc[q][1] = acc[q + 1][1];
+            acc[q][2] = acc[q + 1][2];
+        }
         if (x >= g.nx || y >= g.ny || z >= g.nz) continue;
         float fi[Q];
         pull_f32<D, Q>(A, g, x, y, z, PF, fi);
@@ -423,14 +435,40 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_collide_f32(const float *__rest
         const float n = dn + k.rho0;
         const float pre = k.mGp * sps[c0 + j * STEP];
         float F[3] = {0.f, 0.f, 0.f};
-        F[0] = pre * acc[j][0];
-        F[1] = pre * acc[j][1];
-        if (D == 3) F[2] = pre * acc[j][2];
+        F[0] = pre * s0;
+        F[1] = pre * s1;
+        if (D == 3) F[2] = pre * s2;
         float fo[Q];
         collide<float, D, Q, true>(fi, n, dn, F, k, fo, nullptr, nullptr);
-        const long long ps = ((long long)z * g.nyp + (y + g.oy)) * g.nxp + (x + g.ox);
+        // the node, and on a padded layout its periodic images (ghost
+        // columns, rows, corners): one store loop over the destinations
+        const long long zb = (long long)z * g.nyp;
+        const long long p0 = (zb + (y + g.oy)) * g.nxp + (x + g.ox);
+        long long p1 = 0, p2 = 0, p3 = 0;
+        unsigned m = 1u;
+        if (D == 3 && g.oy > 0) {
+            const int gx = x < GHOST_X ? x + g.nx : (x >= g.nx - GHOST_X ? x - g.nx : INT_MIN);
+            const int gy = y < g.oy ? y + g.ny : (y >= g.ny - g.oy ? y - g.ny : INT_MIN);
+            if (gx != INT_MIN) {
+                p1 = (zb + (y + g.oy)) * g.nxp + (gx + g.ox);
+                m |= 2u;
+            }
+            if (gy != INT_MIN) {
+                p2 = (zb + (gy + g.oy)) * g.nxp + (x + g.ox);
+                m |= 4u;
+                if (gx != INT_MIN) {
+                    p3 = (zb + (gy + g.oy)) * g.nxp + (gx + g.ox);
+                    m |= 8u;
+                }
+            }
+        }
+#pragma unroll 1
+        for (int d = 0; d < 4; ++d) {
+            if (!((m >> d) & 1u)) continue;
+            const long long o = d == 0 ? p0 : (d == 1 ? p1 : (d == 2 ? p2 : p3));
 #pragma unroll
-        for (int i = 0; i < Q; ++i) B[(long long)i * g.Np + ps] = fo[i];
+            for (int i = 0; i < Q; ++i) B[(long long)i * g.Np + o] = fo[i];
+        }
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0)
         flags->step = flags->step + 1;
