@@ -550,8 +550,9 @@ def run_gb300(args, dist, rank, ws):
     # the paper's wide tuned stencils, which the fused kernels do not cover
     # (groups beyond radius 2): Table tab:e4e6_tuning_8 in 3D (N_e = 140, up
     # to (4,0,0), (3,3,0), (2,2,1)) on the same bubble, and in 2D (N_e = 32)
-    # on a 2048^2 lattice; the generic binary32 two-kernel path (psi, then
-    # force + collision), algorithmic bytes 80 + 156 per node
+    # on a 2048^2 lattice; the generic binary32 two-kernel path (psi into a
+    # halo'd field, then force from a shared-memory psi box + collision),
+    # algorithmic bytes 80 + 156 per node
     wide = None
     if not args.no_wide:
         wide = {}
@@ -803,16 +804,23 @@ def run_gb300(args, dist, rank, ws):
         ctx = P.lb_create(P.make_params("D3Q19", (NX, NY, NZ), "fp32", 1.0, G, CONVENTION),
                           rho_pinned.numpy(), None, stream.cuda_stream)
         P.lb_set_stencil(ctx, 3, L.E8_3D.bases, L.E8_3D.weights)
+        ta = time.perf_counter()       # lb_create synchronises: the upload is done
         P.lb_step(ctx, args.steps)
+        P.lb_sync(ctx)
+        tb = time.perf_counter()
         P._check(P._lib.lb_get_fields(P._vp(ctx), P._ptr(rho_out.numpy()), None), "lb_get_fields")
         o2 = P.lb_observables(ctx)
         t1 = time.perf_counter()
         P.lb_destroy(ctx)
         dt = reduce_max(dist, t1 - t0, dev)
+        # where the time goes: the fixed costs (allocation, upload and
+        # initialisation; read-back) against the steps, which they amortise
         e2e = {"value": N * args.steps * ws / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": N * 8 / args.steps,
                "d2h_bytes_per_step": (N * 8 + 88) / args.steps,
-               "seconds": dt, "mass": o2["mass"]}
+               "seconds": dt, "mass": o2["mass"],
+               "phases_s": {"create_upload": ta - t0, "steps": tb - ta, "readback": t1 - tb},
+               "steps_only_mlups": N * args.steps / (tb - ta) / 1e6}
 
     c1 = c2 = None
     if not args.no_configs:

@@ -739,7 +739,11 @@ lb_status lb_get_fields(lb_ctx *c, double *rho, double *u) {
     const long long N = c->g.N;
     if ((size_t)(2 + c->D) * N * sizeof(double) > stage_bytes(c)) return LB_EUNSUPPORTED;
     double *n = stage_ptr(c), *ud = n + 2 * N;
-    cudaError_t e = c->p.precision == LB_FP64 ? f64_fields(c, n, ud, nullptr) : f32_fields(c, n, ud, nullptr);
+    cudaError_t e;
+    if (!u)   // the density alone: no psi, no force
+        e = c->p.precision == LB_FP64 ? f64_density_psi(c, n, nullptr) : f32_density_psi(c, n, nullptr);
+    else
+        e = c->p.precision == LB_FP64 ? f64_fields(c, n, ud, nullptr) : f32_fields(c, n, ud, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "fields kernels");
     if (rho) CK(cudaMemcpyAsync(rho, n, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (u) CK(cudaMemcpyAsync(u, ud, c->D * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -8,8 +8,8 @@ namespace sclbm {
 
 cudaError_t ghosts_refresh(lb_ctx *c) {
     if (!c->padded) return cudaSuccess;
-    const long long total = (long long)c->g.nxp * c->g.nyp * c->g.nz * c->Q;
-    k_ghosts<float><<<grid_for(total), 256, 0, c->stream>>>((float *)c->f[c->cur], c->g, c->Q);
+    const long long rows = (long long)c->g.nyp * c->g.nz * c->Q;   // one warp a row
+    k_ghosts<float><<<grid_for(rows * 32), 256, 0, c->stream>>>((float *)c->f[c->cur], c->g, c->Q);
     c->launches++;
     return cudaGetLastError();
 }

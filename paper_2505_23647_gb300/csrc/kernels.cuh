@@ -55,6 +55,13 @@ __device__ __forceinline__ long long popidx(const Geom &g, int x, int y, int z) 
 }
 
 __device__ __forceinline__ void coords(const Geom &g, long long s, int &x, int &y, int &z) {
+    if (g.N < (1LL << 31)) {   // 32-bit division (a 64-bit one is a long call)
+        const int si = (int)s, qi = si / g.nx;
+        x = si - qi * g.nx;
+        z = qi / g.ny;
+        y = qi - z * g.ny;
+        return;
+    }
     long long q = s / g.nx;
     x = (int)(s - q * g.nx);
     z = (int)(q / g.ny);
@@ -474,7 +481,8 @@ __global__ void __launch_bounds__(CT_X * CT_Y) k_collide_f32(const float *__rest
         flags->step = flags->step + 1;
 }
 
-// Density and psi in binary64 from a state of either precision.
+// Density and psi in binary64 from a state of either precision (psi_out may
+// be null: the density alone).
 template <typename T, int D, int Q, bool SHIFT>
 __global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,
                                 double *__restrict__ n_out, double *__restrict__ psi_out,
@@ -491,7 +499,7 @@ __global__ void k_density_psi64(const T *__restrict__ A, Geom g, double rho0,
         double n = sum_q<double, Q>(fi);
         if (SHIFT) n = n + rho0;
         n_out[s] = n;
-        psi_out[s] = psi_eval<double>(n, pk, &flags->exp_amb);
+        if (psi_out) psi_out[s] = psi_eval<double>(n, pk, &flags->exp_amb);
     }
 }
 
@@ -591,22 +599,31 @@ __global__ void k_set_state(T *__restrict__ A, Geom g, const double *__restrict_
     }
 }
 
-// Refresh the periodic ghost columns/rows of every population plane from
-// the nodes they mirror (padded layouts only).
+// Refresh the periodic ghost images of every population plane from the
+// nodes they mirror (padded layouts only): the GHOST_X columns next to each
+// x edge of every row and, in the ghost rows, columns -GHOST_X .. nx +
+// GHOST_X - 1 (the padding beyond them is never read).  One warp per padded
+// row, rows (i, z, y) of the buffer in order.
 template <typename T>
 __global__ void k_ghosts(T *__restrict__ A, Geom g, int Q) {
-    const long long plane = (long long)g.nxp * g.nyp;
-    const long long total = plane * g.nz * Q;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
-        const long long r = k % plane;
-        const int yp = (int)(r / g.nxp), xp = (int)(r - (long long)yp * g.nxp);
-        const int xl = xp - g.ox, yl = yp - g.oy;
-        if (xl >= 0 && xl < g.nx && yl >= 0 && yl < g.ny) continue;
-        const long long zi = k / plane;   // i * nz + z
-        const long long src = zi * plane + (long long)(wrapi(yl, g.ny) + g.oy) * g.nxp +
-                              (wrapi(xl, g.nx) + g.ox);
-        A[k] = A[src];
+    const long long rows = (long long)g.nyp * g.nz * Q;
+    const int lane = threadIdx.x & 31;
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
+         r += wstride) {
+        const long long zi = r / g.nyp;   // i * nz + z
+        const int yp = (int)(r - zi * g.nyp), yl = yp - g.oy;
+        const int ys = wrapi(yl, g.ny) + g.oy;
+        T *row = A + r * g.nxp + g.ox;
+        const T *src = A + (zi * g.nyp + ys) * g.nxp + g.ox;
+        if (yl >= 0 && yl < g.ny) {   // interior row: the ghost columns
+            if (lane < 2 * GHOST_X) {
+                const int x = lane < GHOST_X ? lane - GHOST_X : g.nx + lane - GHOST_X;
+                row[x] = src[wrapi(x, g.nx)];
+            }
+        } else {   // ghost row: the whole image, ghost columns included
+            for (int x = lane - GHOST_X; x < g.nx + GHOST_X; x += 32) row[x] = src[wrapi(x, g.nx)];
+        }
     }
 }
 
