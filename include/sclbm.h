@@ -418,9 +418,11 @@ lb_status lb_batch_tune(lb_batch *batch, int steps_per_trial, double *ms_out);
  * surface tension sigma_0 (Sec. V A; the Appendix E pressure tensor summed
  * over the lattice is (G'/2) sum_x psi(x) sum_e W(e) psi(x+e)(e_x^2 - e_y^2))
  * or of any loss whose gradient with respect to the state the caller
- * supplies.  An adjoint belongs to one context (any lattice, precision and
- * pseudopotential; LB_EUNSUPPORTED with the F^2 forcing variant); its
- * adjoint variable lam = dL/d(state) has the layout of lb_get_state.
+ * supplies.  An adjoint belongs to one context (any lattice, precision,
+ * pseudopotential and forcing: Guo's, or the F^2 variant, whose extra source
+ * -cw_i (A/tau)(4.5 (xi.F)^2 - 1.5 F.F) adds -cw_i (A/tau)(9 (xi.F) xi - 3 F)
+ * to dS_i/dF); its adjoint variable lam = dL/d(state) has the layout of
+ * lb_get_state.
  *
  * Typical use, with checkpoints every K steps (a checkpoint is lb_get_state
  * / lb_set_state):  step forward saving checkpoints; lb_adjoint_seed_sigma

@@ -7,7 +7,11 @@ from the post-streaming populations g (the state):
     acc = sum_pairs W_a (psi(x + e_a) - psi(x - e_a)) e_a,  F = -G' psi acc,
     j = sum_i g_i xi_i,  u = (j + F/2) / n,
     B_i = g_i - omega (g_i - f_eq_i(n, u)) + S_i(u, F),
-    next state g'_i(x + xi_i) = B_i(x).
+    next state g'_i(x + xi_i) = B_i(x),
+where S_i = cw_i (3 xi.F + 9 (xi.u)(xi.F) - 3 u.F) with Guo's forcing, and
+the F^2 variant (Sec. VI, A = forcing_A, kA = A/tau) subtracts
+cw_i kA (4.5 (xi.F)^2 - 1.5 F.F), so that dS_i/dF gains
+-cw_i kA (9 (xi.F) xi - 3 F).
 With lam' = dL/dg' (same layout as the state), the adjoint gives
 dL/dg, dL/dW (per group) and dL/dG' by the chain rule through each line
 above, read backwards:
@@ -81,14 +85,16 @@ def step_forward(o, g):
     u = (j + 0.5 * F) / n
     om = 1.0 / o.tau
     cwf = (1.0 - 0.5 * om) * w
+    kA = getattr(o, "forcing_A", 0.0) / o.tau
     uu = (u * u).sum(axis=0)
     uF = (u * F).sum(axis=0)
+    FF = (F * F).sum(axis=0)
     out = np.empty_like(g)
     for i in range(Q):
         cu = sum(C[i, a] * u[a] for a in range(D))
         cF = sum(C[i, a] * F[a] for a in range(D))
         feq = w[i] * n * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu)
-        S = cwf[i] * (3 * cF + 9 * cu * cF - 3 * uF)
+        S = cwf[i] * (3 * cF + 9 * cu * cF - 3 * uF - kA * (4.5 * cF * cF - 1.5 * FF))
         B = g[i] - om * (g[i] - feq) + S
         out[i] = _shift(B, -C[i])          # g'_i(x + xi_i) = B_i(x)
     return out
@@ -112,6 +118,7 @@ def step_adjoint(o, g, lam_next):
     u = (j + 0.5 * F) / n
     om = 1.0 / o.tau
     cwf = (1.0 - 0.5 * om) * w
+    kA = getattr(o, "forcing_A", 0.0) / o.tau
     lamB = np.stack([_shift(lam_next[i], C[i]) for i in range(Q)])
     lam_u = np.zeros((3,) + n.shape)
     lam_Fu = np.zeros((3,) + n.shape)
@@ -124,7 +131,8 @@ def step_adjoint(o, g, lam_next):
         for a in range(D):
             dfeq = w[i] * n * (3 * C[i, a] + 9 * cu * C[i, a] - 3 * u[a])
             dSu = cwf[i] * (9 * cF * C[i, a] - 3 * F[a])
-            dSF = cwf[i] * (3 * C[i, a] + 9 * cu * C[i, a] - 3 * u[a])
+            dSF = cwf[i] * (3 * C[i, a] + 9 * cu * C[i, a] - 3 * u[a]
+                            - kA * (9 * cF * C[i, a] - 3 * F[a]))
             lam_u[a] += lamB[i] * (om * dfeq + dSu)
             lam_Fu[a] += lamB[i] * dSF
     lam_j = lam_u / n

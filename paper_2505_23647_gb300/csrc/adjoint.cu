@@ -6,7 +6,8 @@
 //   n = sum g_i, psi = psi(n), acc = sum_pairs W_a (psi(x+e_a) - psi(x-e_a)) e_a,
 //   F = -G' psi acc, j = sum g_i xi_i, u = (j + F/2)/n,
 //   B_i = g_i - omega (g_i - f_eq_i(n,u)) + S_i(u,F),  g'_i(x + xi_i) = B_i(x)
-// (eqs. lbm, omega_i, f_eq, GuoForcing, sc_f).  Going backwards through it
+// (eqs. lbm, omega_i, f_eq, GuoForcing, sc_f; the F^2 variant of Sec. VI
+// subtracts cw_i (A/tau)(4.5 (xi.F)^2 - 1.5 F.F) from S_i).  Going backwards through it
 // with lam' = dL/dg':
 //   lamB_i(x) = lam'_i(x + xi_i);
 //   lam_u = sum_i lamB_i (omega df_eq_i/du + dS_i/du), lam_n|u = omega sum_i lamB_i df_eq_i/dn,
@@ -80,7 +81,7 @@ __global__ void k_adj_a(const double *__restrict__ st, const double *__restrict_
                         double *__restrict__ lacc, double *__restrict__ lpsi,
                         double *__restrict__ gnode) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const double om = k.omega;
+    const double om = k.omega, kA = k.kA;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.N; s += stride) {
         int x, y, z;
         coords(g, s, x, y, z);
@@ -122,7 +123,9 @@ __global__ void k_adj_a(const double *__restrict__ st, const double *__restrict_
                 const double c = cvel<Q>(i, a);
                 const double dfeq = w * n * (3.0 * c + 9.0 * cu * c - 3.0 * u[a]);
                 const double dSu = cw * (9.0 * cF * c - 3.0 * F[a]);
-                const double dSF = cw * (3.0 * c + 9.0 * cu * c - 3.0 * u[a]);
+                double dSF = cw * (3.0 * c + 9.0 * cu * c - 3.0 * u[a]);
+                // F^2 variant: S_i gains -cw kA (4.5 cF^2 - 1.5 F.F)
+                if (kA != 0.0) dSF -= cw * kA * (9.0 * cF * c - 3.0 * F[a]);
                 lu[a] += lb[i] * (om * dfeq + dSu);
                 lF[a] += lb[i] * dSF;
             }
@@ -484,7 +487,7 @@ lb_status lb_adjoint_create(lb_ctx *c, lb_adjoint **out) {
     *out = nullptr;
     if (!c) return LB_EINVAL;
     if (!c->stencil_set) return LB_ESTATE;
-    if (c->p.forcing_A != 0.0 || c->n_groups > adj::MAXG) return LB_EUNSUPPORTED;
+    if (c->n_groups > adj::MAXG) return LB_EUNSUPPORTED;
     lb_adjoint *a = new lb_adjoint();
     a->c = c;
     a->D = c->D;

@@ -554,8 +554,13 @@ __global__ void k_init(T *__restrict__ A, Geom g, const double *__restrict__ rho
         const double n = rho[s];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double cu = cdot<Q, D, double>(i, us);
-            double f = (k.w[i] * n) * (((1.0 + 3.0 * cu) + 4.5 * (cu * cu)) - 1.5 * uu);
+            double f;
+            if (u) {
+                const double cu = cdot<Q, D, double>(i, us);
+                f = (k.w[i] * n) * (((1.0 + 3.0 * cu) + 4.5 * (cu * cu)) - 1.5 * uu);
+            } else {   // u = 0: the bracket is exactly 1 (the same value, fewer binary64 operations)
+                f = k.w[i] * n;
+            }
             if (SHIFT) f = f - k.w[i] * k.rho0;
             A[(long long)i * g.Np +
               popidx(g, x - cvel<Q>(i, 0), y - cvel<Q>(i, 1), z - cvel<Q>(i, 2))] = (T)f;

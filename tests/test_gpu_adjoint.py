@@ -3,8 +3,9 @@
 oracle's forward step) and against finite differences of the GPU's own
 forward runs; checkpointing changes nothing; the torch.autograd.Function
 returns the same gradient; losses on the density (liquid/gas density ratio,
-interface width) differentiate the same way; and a gradient solve of the paper's surface
-tension knob (Table tab:e4_tuning_6, sigma0_hat) hits a target sigma_0."""
+interface width) differentiate the same way; the F^2 forcing variant too; and a
+gradient solve of the paper's surface tension knob (Table tab:e4_tuning_6,
+sigma0_hat) hits a target sigma_0."""
 from fractions import Fraction as Fr
 
 import numpy as np
@@ -61,6 +62,32 @@ def test_gpu_adjoint_matches_oracle_adjoint(lattice, shape, st, tau, G, conv, ep
     assert _rel(dW, dW_o) < 1e-10, (dW, dW_o)
     assert abs(dG - dG_o) < 1e-10 * abs(dG_o)
     assert _rel(lam0.reshape(lam_o.shape), lam_o) < 1e-10
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,steps,A,precision", [
+    ("D2Q9", (24, 5), L.E8_2D, 1.0, -3.0, 12, 0.25, "fp64"),
+    ("D3Q19", (20, 4, 3), L.E4_3D, 0.8, -4.0, 8, 0.6, "fp64"),
+    ("D2Q9", (24, 5), L.E8_2D, 1.0, -3.0, 12, 0.25, "fp32"),
+])
+def test_f2_forcing_adjoint_matches_oracle_adjoint(lattice, shape, st, tau, G, steps, A, precision):
+    """The F^2 variant (Sec. VI): the GPU adjoint against the oracle's (its
+    F^2 terms pinned to finite differences of the C oracle on the CPU)."""
+    lat = P.Lattice(lattice, shape, _rho(shape), st.bases, st.weights, precision=precision,
+                    tau=tau, G=G, forcing_A=A)
+    g0 = lat.state()
+    sigma, dW, dG, lam0 = AD.sigma_and_gradient(lat, steps, checkpoint_every=4)
+    lat.close()
+    nz = shape[2] if len(shape) > 2 else 1
+    o = oracle.Oracle(lattice, (nz, shape[1], shape[0]), st.groups, tau=tau, G=G, forcing_A=A)
+    s_o, lam_o, dW_o, dGp_o = OAD.gradient(o, g0.reshape((o.Q, nz, shape[1], shape[0])), steps, 2)
+    if precision == "fp64":
+        assert abs(sigma - s_o) < 1e-12 * abs(s_o)
+        assert _rel(dW, dW_o) < 1e-10, (dW, dW_o)
+        assert abs(dG - dGp_o) < 1e-10 * abs(dGp_o)
+        assert _rel(lam0.reshape(lam_o.shape), lam_o) < 1e-10
+    else:   # binary32 forward states: the gradient to binary32 accuracy
+        assert abs(sigma - s_o) < 1e-5 * abs(s_o)
+        assert _rel(dW, dW_o) < 1e-3, (dW, dW_o)
 
 
 def test_checkpointing_changes_nothing():

@@ -18,16 +18,16 @@ CASES = [
 ]
 
 
-def _setup(lattice, shape, st, tau, G, conv):
+def _setup(lattice, shape, st, tau, G, conv, A=0.0):
     nz, ny, nx = shape
     rho = L.tanh_slab(nx, ny, nz, nx // 4, 3 * nx // 4, 0.456, 2.25, 2.0)
-    o = oracle.Oracle(lattice, shape, st.groups, tau=tau, G=G, convention=conv)
+    o = oracle.Oracle(lattice, shape, st.groups, tau=tau, G=G, convention=conv, forcing_A=A)
     o.init_equilibrium(rho)
     return o
 
 
-def _sigma_after(lattice, shape, groups, tau, G, conv, g0, steps):
-    o = oracle.Oracle(lattice, shape, groups, tau=tau, G=G, convention=conv)
+def _sigma_after(lattice, shape, groups, tau, G, conv, g0, steps, A=0.0):
+    o = oracle.Oracle(lattice, shape, groups, tau=tau, G=G, convention=conv, forcing_A=A)
     o.f = g0.copy()
     o.step(steps)
     return AD.sigma_flat(o, o.f, 2)[0]
@@ -126,3 +126,55 @@ def test_density_functional_gradient_matches_finite_differences(lattice, shape, 
     fd = (fn(_n_after(lattice, shape, st.groups, tau, G + h, conv, g0, steps))[0] -
           fn(_n_after(lattice, shape, st.groups, tau, G - h, conv, g0, steps))[0]) / (2 * h)
     assert abs(dGp - fd) < 1e-6 * abs(fd) + 1e-9
+
+
+# the F^2 forcing variant (Sec. VI): the source term gains
+# -cw_i (A/tau) (4.5 (xi.F)^2 - 1.5 F.F); A = 0.25 and 0.6
+CASES_F2 = [
+    ("D2Q9", (1, 5, 24), L.E8_2D, 1.0, -3.0, "literal", 10, 0.25),
+    ("D3Q19", (3, 4, 20), L.E4_3D, 0.8, -4.0, "literal", 6, 0.6),
+]
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,steps,A", CASES_F2)
+def test_f2_numpy_forward_matches_c_oracle(lattice, shape, st, tau, G, conv, steps, A):
+    o = _setup(lattice, shape, st, tau, G, conv, A)
+    g = o.f.copy()
+    for _ in range(3):
+        g = AD.step_forward(o, g)
+    o.step(3)
+    assert np.max(np.abs(g - o.f)) < 1e-14
+    # the variant changes the step (a dropped term would pass the first check
+    # only if the F^2 source vanished)
+    o0 = _setup(lattice, shape, st, tau, G, conv, 0.0)
+    o0.step(3)
+    assert np.max(np.abs(o0.f - o.f)) > 1e-8
+
+
+@pytest.mark.parametrize("lattice,shape,st,tau,G,conv,steps,A", CASES_F2)
+def test_f2_adjoint_gradient_matches_finite_differences(lattice, shape, st, tau, G, conv, steps, A):
+    o = _setup(lattice, shape, st, tau, G, conv, A)
+    g0 = o.f.copy()
+    sigma, lam, dW, dGp = AD.gradient(o, g0, steps, 2)
+    assert abs(sigma - _sigma_after(lattice, shape, st.groups, tau, G, conv, g0, steps, A)) < 1e-13
+    for q, (b, wq) in enumerate(st.groups):
+        h = 1e-6 * float(wq)
+        gp = [(bb, float(ww) + (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        gm = [(bb, float(ww) - (h if k == q else 0.0)) for k, (bb, ww) in enumerate(st.groups)]
+        fd = (_sigma_after(lattice, shape, gp, tau, G, conv, g0, steps, A) -
+              _sigma_after(lattice, shape, gm, tau, G, conv, g0, steps, A)) / (2 * h)
+        assert abs(dW[q] - fd) < 1e-6 * max(abs(fd), 1e-3 * abs(sigma) / float(wq)), (q, dW[q], fd)
+    h = 1e-6 * abs(G)
+    fd = (_sigma_after(lattice, shape, st.groups, tau, G + h, conv, g0, steps, A) -
+          _sigma_after(lattice, shape, st.groups, tau, G - h, conv, g0, steps, A)) / (2 * h)
+    assert abs(dGp - fd) < 1e-6 * abs(fd), (dGp, fd)
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        idx = tuple(int(rng.integers(0, s)) for s in g0.shape)
+        h = 1e-4 * abs(g0[idx])
+        gp, gm = g0.copy(), g0.copy()
+        gp[idx] += h
+        gm[idx] -= h
+        fd = (_sigma_after(lattice, shape, st.groups, tau, G, conv, gp, steps, A) -
+              _sigma_after(lattice, shape, st.groups, tau, G, conv, gm, steps, A)) / (2 * h)
+        assert abs(lam[idx] - fd) < 1e-6 * abs(fd) + 1e-10, (idx, lam[idx], fd)
