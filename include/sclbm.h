@@ -64,7 +64,7 @@ typedef enum lb_status {
     LB_ENOMEM = 2,        /* device or host allocation failed */
     LB_ECUDA = 3,         /* a CUDA runtime call failed (see lb_last_cuda_error) */
     LB_EUNSTABLE = 4,     /* a node had n <= 0 or NaN (see lb_obs.error_step) */
-    LB_EUNSUPPORTED = 5,  /* valid request this build does not cover */
+    LB_EUNSUPPORTED = 5,  /* valid request the library does not cover */
     LB_ESTATE = 6         /* call out of order, e.g. lb_step before lb_set_stencil */
 } lb_status;
 

@@ -313,7 +313,7 @@ const char *lb_status_str(lb_status s) {
         case LB_ENOMEM: return "LB_ENOMEM: out of memory";
         case LB_ECUDA: return "LB_ECUDA: CUDA runtime error";
         case LB_EUNSTABLE: return "LB_EUNSTABLE: density check failed (n <= 0 or NaN)";
-        case LB_EUNSUPPORTED: return "LB_EUNSUPPORTED: not covered by this build";
+        case LB_EUNSUPPORTED: return "LB_EUNSUPPORTED: not covered by the library";
         case LB_ESTATE: return "LB_ESTATE: call out of order";
     }
     return "unknown lb_status";
