@@ -24,7 +24,7 @@
 #include <cstring>
 #include <vector>
 
-#include "fusedcommon.cuh"
+#include "collide_tiled.cuh"
 
 namespace sclbm {
 namespace b2 {
@@ -447,6 +447,26 @@ static void inst_from_ctx(const lb_ctx *c, b2::Inst *I) {
         I->c9[k] = (float)(9.0 * cw);
         I->c3[k] = (float)(3.0 * cw);
     }
+}
+
+// D2Q9 collision of one node for the generic tiled kernel: the batch
+// kernels' pair-symmetric collide9 with the lattice's mass-exact constants
+struct Col9 {
+    b2::Inst I;
+    __device__ __forceinline__ void operator()(const float *fi, float dn, float, const float *F,
+                                               float *fo) const {
+        if (I.mhkA != 0.f) b2::collide9<true>(fi, dn, F[0], F[1], I, fo);
+        else b2::collide9<false>(fi, dn, F[0], F[1], I, fo);
+    }
+};
+
+// the generic D2Q9 step's collision (after k_psi_f32 has filled psi)
+void f32_collide2d_tiled(lb_ctx *c, const float *A, float *B, const float *psi) {
+    Col9 col;
+    inst_from_ctx(c, &col.I);
+    const dim3 grid((c->g.nx + CT_X - 1) / CT_X, (c->g.ny + CT_Y2 - 1) / CT_Y2, 1);
+    k_collide_f32<2, 9><<<grid, dim3(CT_X, CT_Y), ct_box(2) * sizeof(float), c->stream>>>(
+        A, B, psi, c->g, c->pfast, consts_as<float>(c->k), col, c->flags);
 }
 
 cudaError_t f32_fused2d_step(lb_ctx *c) {
