@@ -183,7 +183,9 @@ lb_status lb_expand_stencil(int dim, int n_groups, const int *base_vectors,
  * float64; u_init: host [D][N] float64 or NULL.  cuda_stream: a
  * cudaStream_t all work of the context is ordered on, or NULL for a stream
  * the context creates.  On success *out owns device memory until
- * lb_destroy.  LB_EINVAL for bad parameters, LB_ENOMEM, LB_ECUDA. */
+ * lb_destroy.  LB_EINVAL for bad parameters (checked on the host) or an
+ * initial density that is not positive and finite (checked on the device
+ * after the upload; nothing is left allocated), LB_ENOMEM, LB_ECUDA. */
 lb_status lb_create(const lb_params *p, const double *rho_init,
                     const double *u_init, void *cuda_stream, lb_ctx **out);
 

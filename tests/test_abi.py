@@ -90,15 +90,6 @@ def test_invalid_params_rejected_on_host(P, field, value):
     assert ei.value.status == P.LB_EINVAL
 
 
-def test_nonpositive_density_rejected_on_host(P):
-    p = P.make_params("D2Q9", (4, 4))
-    rho = np.ones(16)
-    rho[3] = 0.0
-    with pytest.raises(P.LbError) as ei:
-        P.lb_create(p, rho)
-    assert ei.value.status == P.LB_EINVAL
-
-
 def test_laplace_and_tolman_fits_match_the_oracle_fits(P):
     """lb_fit_laplace / lb_fit_tolman are host arithmetic: the same lines as
     the oracle's laplace_sigma / tolman_curved_fit on made-up results."""

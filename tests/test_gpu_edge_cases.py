@@ -4,7 +4,8 @@ Periodic lattices smaller than the stencil (1 x 1, 1 x 1 x 1, 2 x 3, 3 x 2 x 2,
 a single row or column) make every neighbour an image of the node itself or
 of a few nodes: binary64 must still match the oracle bit for bit, binary32
 within its tolerance; a uniform state is a fixed point to rounding; a
-zero-step call changes nothing."""
+zero-step call changes nothing; an initial density that is not positive
+and finite is rejected by lb_create."""
 import numpy as np
 import pytest
 
@@ -83,3 +84,18 @@ def test_uniform_state_is_a_fixed_point(lattice, shape, st, precision):
     lat.step(0)
     assert np.array_equal(lat.state(), f1)
     lat.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
+def test_initial_density_not_positive_and_finite_is_rejected(precision, bad):
+    """lb_create checks the uploaded densities on the device: LB_EINVAL, and
+    a valid creation afterwards still works (nothing left behind)."""
+    p = P.make_params("D3Q19", (32, 8, 9), precision)
+    rho = np.ones(32 * 8 * 9)
+    rho[123] = bad
+    with pytest.raises(P.LbError) as ei:
+        P.lb_create(p, rho)
+    assert ei.value.status == P.LB_EINVAL
+    ctx = P.lb_create(p, np.ones(32 * 8 * 9))
+    P.lb_destroy(ctx)
