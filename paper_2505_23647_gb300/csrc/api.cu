@@ -465,11 +465,11 @@ lb_status lb_create(const lb_params *p, const double *rho_init, const double *u_
     k_check_rho<<<gb, 256, 0, c->stream>>>(rho_d, N, bad_d);
     e = p->precision == LB_FP64 ? f64_init(c, rho_d, u_d) : f32_init(c, rho_d, u_d);
     if (e != cudaSuccess) return fail(cuda_fail(e, "init kernel"));
+    unsigned int bad = 0;
+    e = cudaMemcpyAsync(&bad, bad_d, sizeof bad, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(flag)"));
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "lb_create sync"));
-    unsigned int bad = 0;
-    e = cudaMemcpy(&bad, bad_d, sizeof bad, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpy(flag)"));
     if (bad) return fail(LB_EINVAL);
     *out = c;
     return LB_OK;
