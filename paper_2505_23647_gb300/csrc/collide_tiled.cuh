@@ -27,9 +27,10 @@ struct Col19 {
 // folded weights are read once for NPT nodes; per node the operations are
 // those of force_fast in the same order, so the result is bit for bit the
 // one the global-memory form gives.  Then it pulls, collides (Col: the
-// collision of one node, below) and stores its
-// nodes one by one, with their periodic images on a padded layout (as the
-// fused kernels write them), so no separate ghost refresh follows the step.
+// collision of one node: Col19 here, the D2Q9 one in batch2d.cu) and
+// stores its nodes one by one, with their periodic images on a padded
+// layout (as the fused kernels write them), so no separate ghost refresh
+// follows the step.
 // Requires the halo'd psi field (fewer than 2^31 of its nodes) and dynamic
 // shared memory of ct_box(D) floats.
 template <int D, int Q, class Col>
