@@ -90,6 +90,24 @@ def test_f2_forcing_adjoint_matches_oracle_adjoint(lattice, shape, st, tau, G, s
         assert _rel(dW, dW_o) < 1e-3, (dW, dW_o)
 
 
+def test_graph_replay_changes_nothing():
+    """Segments after the first replay a captured graph of the run; with
+    per-kernel timing on, every segment runs directly: the same bits."""
+    lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
+    out = []
+    for timing in (False, True):
+        lat = _lat(lattice, shape, st, tau, G, conv, eps, precision="fp32")
+        if timing:
+            P.lb_timing(lat.ctx, 1)
+        out.append(AD.sigma_and_gradient(lat, 24, checkpoint_every=6))
+        f = lat.state()
+        out[-1] = out[-1] + (f,)
+        lat.close()
+    (s0, w0, g0, l0, f0), (s1, w1, g1, l1, f1) = out
+    assert s0 == s1 and g0 == g1
+    assert np.array_equal(w0, w1) and np.array_equal(l0, l1) and np.array_equal(f0, f1)
+
+
 def test_checkpointing_changes_nothing():
     lattice, shape, st, tau, G, conv, eps, _ = CASES[0]
     res = []
